@@ -1,0 +1,206 @@
+"""ctypes front end of the C oracle ``pf_oracle.c`` (test infrastructure only).
+
+The C file is compiled on first use with ``gcc -O2 -ffp-contract=off`` into
+``oracle/_build/liboracle.so``; ``build()`` does it explicitly.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import subprocess
+import threading
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "pf_oracle.c"
+_LIB = _HERE / "_build" / "liboracle.so"
+_lock = threading.Lock()
+_lib = None
+
+OK, BUDGET, NONFINITE = 0, 1, 2
+DEFAULT_BUDGET = 1 << 20
+
+
+def build(force: bool = False) -> Path:
+    """Compile the oracle shared library (no FMA contraction)."""
+    if force or not _LIB.exists() or _LIB.stat().st_mtime < _SRC.stat().st_mtime:
+        _LIB.parent.mkdir(parents=True, exist_ok=True)
+        tmp = _LIB.with_suffix(f".{os.getpid()}.tmp")
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared",
+                               "-std=gnu11", "-o", str(tmp), str(_SRC), "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _bind(path: Path) -> ct.CDLL:
+    lib = ct.CDLL(str(path))
+    P = ct.c_void_p
+    lib.orc_philox4x32_10.argtypes = [P, P, P]
+    lib.orc_philox4x32_10.restype = None
+    lib.orc_resample_systematic.argtypes = [P, ct.c_int32, ct.c_uint64, P]
+    lib.orc_resample_systematic.restype = None
+    lib.orc_pf_loglik.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, ct.c_int64, ct.c_int32, P,
+                                  P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P, ct.c_int32,
+                                  ct.c_uint64, ct.c_uint64, P, P, P, P, P, P]
+    lib.orc_pf_loglik.restype = ct.c_int
+    lib.orc_ssa_paths.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, ct.c_int32, P, P,
+                                  ct.c_int32, ct.c_int64, ct.c_uint64, ct.c_uint64, P, P, P]
+    lib.orc_ssa_paths.restype = ct.c_int
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = _bind(_LIB)
+    return _lib
+
+
+def compile_variant(source_text: str, out_dir: Path) -> "Oracle":
+    """Compile a modified copy of the oracle source (used by the mutation tests
+    to show that the pins detect planted mistakes) and bind it."""
+    out_dir = Path(out_dir)
+    src = out_dir / "variant.c"
+    so = out_dir / "libvariant.so"
+    src.write_text(source_text)
+    subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=gnu11",
+                           "-o", str(so), str(src), "-lm"])
+    return Oracle(_bind(so))
+
+
+def source_text() -> str:
+    return _SRC.read_text()
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Oracle:
+    """The oracle's entry points bound to one compiled library."""
+
+    def __init__(self, lib: ct.CDLL):
+        self._lib = lib
+
+    def philox4x32_10(self, ctr, key) -> np.ndarray:
+        """Philox4x32-10 block for one (counter[4], key[2]) pair, as uint32[4]."""
+        lib = self._lib
+        c = _c(ctr, np.uint32)
+        k = _c(key, np.uint32)
+        out = np.zeros(4, np.uint32)
+        lib.orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
+        return out
+
+
+    def resample_systematic(self, q, r64: int) -> np.ndarray:
+        """Ancestor indices of integer-weight systematic resampling."""
+        lib = self._lib
+        q = _c(q, np.uint64)
+        anc = np.zeros(len(q), np.int32)
+        lib.orc_resample_systematic(_ptr(q), len(q), ct.c_uint64(int(r64)), _ptr(anc))
+        return anc
+
+
+    def pf_loglik(self, net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, seed: int,
+                      budget: int = DEFAULT_BUDGET, theta_ids=None,
+                      want_final_states: bool = False):
+        """Filter log-likelihood of every theta row.
+
+        net: {"reactants": [R][U], "products": [R][U], "rate_index": [R] or None}
+        y: [T][K][P].  Returns a dict with loglik[M], status[M], ll_traj[M][T],
+        events[M][T], digest[M][T] and optionally final_states[M][T][N][U].
+        """
+        lib = self._lib
+        reac = _c(net["reactants"], np.int32)
+        prod = _c(net["products"], np.int32)
+        R, U = reac.shape
+        ri = net.get("rate_index")
+        ri = None if ri is None else _c(ri, np.int32)
+        th = _c(thetas, np.float64)
+        if th.ndim == 1:
+            th = th[None, :]
+        M, d = th.shape
+        ids = None if theta_ids is None else _c(theta_ids, np.int64)
+        x0 = _c(x0, np.int32)
+        ts = _c(obs_times, np.float64)
+        yy = _c(y, np.float64)
+        T, K, P = yy.shape
+        Cm = _c(C, np.float64).reshape(P, U)
+        sg = _c(sigma, np.float64).reshape(P)
+        N = int(n_particles)
+        out = {
+            "loglik": np.zeros(M, np.float64),
+            "status": np.zeros(M, np.uint8),
+            "ll_traj": np.zeros((M, T), np.float64),
+            "events": np.zeros((M, T), np.uint64),
+            "digest": np.zeros((M, T), np.uint64),
+        }
+        fs = np.zeros((M, T, N, U), np.int32) if want_final_states else None
+        rc = lib.orc_pf_loglik(U, R, _ptr(reac), _ptr(prod), _ptr(ri), _ptr(th), M, d, _ptr(ids),
+                               _ptr(x0), _ptr(ts), K, _ptr(yy), T, P, _ptr(Cm), _ptr(sg), N,
+                               ct.c_uint64(int(seed)), ct.c_uint64(int(budget)),
+                               _ptr(out["loglik"]), _ptr(out["status"]), _ptr(out["ll_traj"]),
+                               _ptr(out["events"]), _ptr(out["digest"]), _ptr(fs))
+        if rc != 0:
+            raise ValueError(f"oracle rejected the problem (code {rc})")
+        if fs is not None:
+            out["final_states"] = fs
+        return out
+
+
+    def ssa_paths(self, net: dict, theta, x0, times, n_paths: int, seed: int,
+                      budget: int = DEFAULT_BUDGET):
+        """Independent direct-method paths; returns (states[n][K][U], fired[n], status[n])."""
+        lib = self._lib
+        reac = _c(net["reactants"], np.int32)
+        prod = _c(net["products"], np.int32)
+        R, U = reac.shape
+        ri = net.get("rate_index")
+        ri = None if ri is None else _c(ri, np.int32)
+        th = _c(theta, np.float64).reshape(-1)
+        x0 = _c(x0, np.int32)
+        ts = _c(times, np.float64)
+        K = len(ts)
+        states = np.zeros((n_paths, K, U), np.int32)
+        fired = np.zeros(n_paths, np.uint64)
+        status = np.zeros(n_paths, np.uint8)
+        rc = lib.orc_ssa_paths(U, R, _ptr(reac), _ptr(prod), _ptr(ri), _ptr(th), len(th), _ptr(x0),
+                               _ptr(ts), K, n_paths, ct.c_uint64(int(seed)), ct.c_uint64(int(budget)),
+                               _ptr(states), _ptr(fired), _ptr(status))
+        if rc != 0:
+            raise ValueError(f"oracle rejected the problem (code {rc})")
+        return states, fired, status
+
+
+_default = None
+
+
+def default() -> Oracle:
+    global _default
+    if _default is None:
+        _default = Oracle(_load())
+    return _default
+
+
+def philox4x32_10(ctr, key):
+    return default().philox4x32_10(ctr, key)
+
+
+def resample_systematic(q, r64: int):
+    return default().resample_systematic(q, r64)
+
+
+def pf_loglik(*args, **kwargs):
+    return default().pf_loglik(*args, **kwargs)
+
+
+def ssa_paths(*args, **kwargs):
+    return default().ssa_paths(*args, **kwargs)

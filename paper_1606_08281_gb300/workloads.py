@@ -1,0 +1,230 @@
+"""Seeded synthetic workloads: networks, parameter batches and observations.
+
+This module holds no arithmetic of the likelihood method itself.  It builds
+network descriptions (stoichiometry tables), draws candidate parameter vectors
+theta from log-uniform priors, and loads the stored observed trajectories.  The
+observed trajectories ``y`` are inputs; they were written once by
+``tests/golden/make_observations.py`` (which simulates the network at a fixed
+theta* with the test oracle and adds Gaussian noise) and are read here from
+``tests/golden/observations.json``.
+
+Networks follow the paper's notation (Sec. "Chemical Reaction Networks"):
+reaction r consumes p_ru and produces q_ru molecules of species u; its rate
+constant is theta[rate_index[r]].  Shapes:
+  reactants, products: int32 [R][U]; rate_index: int32 [R] or None (= r).
+
+Workloads (sizes (U, R, P, K, T, M, N)):
+  birth_death     (1, 2, 1, 20, 1, 200, 100)
+  gene_expression (2, 4, 1, 50, 10, 4096, 1000)
+  cascade         (10, 20, 3, 100, 16, 16384, 512)
+"""
+from __future__ import annotations
+
+import json
+from dataclasses import dataclass, field
+from pathlib import Path
+
+import numpy as np
+
+REPO_ROOT = Path(__file__).resolve().parent.parent
+OBSERVATIONS_PATH = REPO_ROOT / "tests" / "golden" / "observations.json"
+
+
+# --------------------------------------------------------------------------
+# networks
+# --------------------------------------------------------------------------
+def birth_death_network() -> dict:
+    """0 -> X (k1), X -> 0 (k2 x): the paper's birth-death example."""
+    return {
+        "name": "birth_death",
+        "species": ["X"],
+        "reactants": np.array([[0], [1]], np.int32),
+        "products": np.array([[1], [0]], np.int32),
+        "rate_index": None,
+    }
+
+
+def gene_expression_network() -> dict:
+    """Two-stage gene expression: 0->M (k_m), M->0 (g_m M), M->M+P (k_p M), P->0 (g_p P)."""
+    return {
+        "name": "gene_expression",
+        "species": ["mRNA", "protein"],
+        "reactants": np.array([[0, 0], [1, 0], [1, 0], [0, 1]], np.int32),
+        "products": np.array([[1, 0], [0, 0], [1, 1], [0, 0]], np.int32),
+        "rate_index": None,
+    }
+
+
+def cascade_network(seed: int = 3000, U: int = 10, n0: int = 4, n1: int = 10, n2: int = 6) -> dict:
+    """Seeded synthetic signalling cascade with mass-action orders <= 2.
+
+    Rules: every species is consumed by one first-order reaction that either
+    converts it into the next species of a random chain or degrades it (the
+    chain's last species always degrades, so every species drains); order-2
+    reactions A + B -> C or A + B -> 0 conserve or destroy mass; order-0
+    reactions produce one molecule.  Every species is a product of at least one
+    reaction.  Returns the network plus the rate bounds per reaction.
+    """
+    rng = np.random.default_rng(seed)
+    R = n0 + n1 + n2
+    assert n1 == U, "one first-order reaction per species"
+    reac = np.zeros((R, U), np.int32)
+    prod = np.zeros((R, U), np.int32)
+    order = np.zeros(R, np.int32)
+    r = 0
+    for _ in range(n0):                                # 0 -> X_v
+        prod[r, rng.integers(U)] = 1
+        order[r] = 0
+        r += 1
+    chain = rng.permutation(U)
+    for i, u in enumerate(chain):                      # X_u -> X_next or X_u -> 0
+        reac[r, u] = 1
+        if i + 1 < U and rng.random() < 0.6:
+            prod[r, chain[i + 1]] = 1
+        order[r] = 1
+        r += 1
+    for _ in range(n2):                                # X_a + X_b -> X_c or -> 0
+        a, b = rng.integers(U), rng.integers(U)
+        reac[r, a] += 1
+        reac[r, b] += 1
+        if rng.random() < 0.7:
+            prod[r, rng.integers(U)] = 1
+        order[r] = 2
+        r += 1
+    # repair: every species must be produced by some reaction
+    for u in range(U):
+        if prod[:, u].sum() == 0:
+            cands = [rr for rr in range(R) if order[rr] in (0, 2)]
+            rr = cands[int(rng.integers(len(cands)))]
+            prod[rr, :] = 0
+            prod[rr, u] = 1
+    for u in range(U):
+        assert reac[:, u].sum() > 0 and prod[:, u].sum() > 0
+    bounds = {0: (0.1, 100.0), 1: (1e-3, 1.0), 2: (1e-5, 1e-2)}
+    lo = np.array([bounds[int(o)][0] for o in order])
+    hi = np.array([bounds[int(o)][1] for o in order])
+    return {
+        "name": "cascade",
+        "species": [f"S{u}" for u in range(U)],
+        "reactants": reac,
+        "products": prod,
+        "rate_index": None,
+        "order": order,
+        "prior_lo": lo,
+        "prior_hi": hi,
+    }
+
+
+# --------------------------------------------------------------------------
+# parameter draws
+# --------------------------------------------------------------------------
+def log_uniform(rng: np.random.Generator, lo, hi, M: int) -> np.ndarray:
+    """M rows of independent log-uniform draws between lo[i] and hi[i]."""
+    lo = np.log(np.asarray(lo, float))
+    hi = np.log(np.asarray(hi, float))
+    return np.exp(rng.uniform(lo, hi, size=(M, len(lo))))
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+@dataclass
+class Workload:
+    name: str
+    net: dict
+    x0: np.ndarray            # int32 [U]
+    obs_times: np.ndarray     # float64 [K]
+    C: np.ndarray             # float64 [P][U]
+    sigma: np.ndarray         # float64 [P]
+    prior_lo: np.ndarray      # float64 [d]
+    prior_hi: np.ndarray      # float64 [d]
+    theta_star: np.ndarray    # float64 [d] (data-generating)
+    T: int
+    M: int
+    N: int
+    theta_seed: int
+    filter_seed: int
+    data_seed: int
+    y: np.ndarray | None = field(default=None)   # float64 [T][K][P]
+
+    @property
+    def U(self) -> int:
+        return int(self.net["reactants"].shape[1])
+
+    @property
+    def R(self) -> int:
+        return int(self.net["reactants"].shape[0])
+
+    @property
+    def K(self) -> int:
+        return int(len(self.obs_times))
+
+    @property
+    def P(self) -> int:
+        return int(self.C.shape[0])
+
+    def thetas(self, M: int | None = None) -> np.ndarray:
+        """The workload's seeded theta batch (first M rows of the full batch)."""
+        rng = np.random.default_rng(self.theta_seed)
+        full = log_uniform(rng, self.prior_lo, self.prior_hi, self.M)
+        return np.ascontiguousarray(full[: (self.M if M is None else M)])
+
+    def observations(self) -> np.ndarray:
+        if self.y is None:
+            self.y = load_observations(self.name)
+        return self.y
+
+    def subset(self, T: int | None = None, K: int | None = None) -> "Workload":
+        """A copy restricted to the first T trajectories and first K observation times."""
+        T = self.T if T is None else T
+        K = self.K if K is None else K
+        w = Workload(**{**self.__dict__})
+        w.T = T
+        w.obs_times = self.obs_times[:K].copy()
+        w.y = self.observations()[:T, :K, :].copy()
+        return w
+
+
+def birth_death() -> Workload:
+    return Workload(
+        name="birth_death", net=birth_death_network(), x0=np.array([10], np.int32),
+        obs_times=np.arange(1, 21, dtype=np.float64), C=np.array([[1.0]]),
+        sigma=np.array([1.0]), prior_lo=np.array([1.0, 0.05]), prior_hi=np.array([50.0, 1.0]),
+        theta_star=np.array([10.0, 0.2]), T=1, M=200, N=100,
+        data_seed=1001, theta_seed=1002, filter_seed=1003)
+
+
+def gene_expression() -> Workload:
+    ts = np.array([0.1, 0.1, 1.0, 0.01])
+    return Workload(
+        name="gene_expression", net=gene_expression_network(), x0=np.array([0, 0], np.int32),
+        obs_times=5.0 * np.arange(1, 51, dtype=np.float64), C=np.array([[0.0, 1.0]]),
+        sigma=np.array([5.0]), prior_lo=ts / 10.0, prior_hi=ts * 10.0, theta_star=ts, T=10, M=4096, N=1000,
+        data_seed=2001, theta_seed=2002, filter_seed=2003)
+
+
+def cascade() -> Workload:
+    net = cascade_network(3000)
+    rng = np.random.default_rng(3004)
+    x0 = rng.integers(0, 101, size=10).astype(np.int32)
+    theta_star = log_uniform(np.random.default_rng(3005), net["prior_lo"], net["prior_hi"], 1)[0]
+    C = np.zeros((3, 10))
+    C[0, 0] = C[1, 1] = C[2, 2] = 1.0
+    return Workload(
+        name="cascade", net=net, x0=x0, obs_times=np.arange(1, 101, dtype=np.float64), C=C,
+        sigma=np.array([2.0, 2.0, 2.0]), prior_lo=net["prior_lo"], prior_hi=net["prior_hi"],
+        theta_star=theta_star, T=16, M=16384, N=512,
+        data_seed=3001, theta_seed=3002, filter_seed=3003)
+
+
+WORKLOADS = {"birth_death": birth_death, "gene_expression": gene_expression, "cascade": cascade}
+
+
+def get(name: str) -> Workload:
+    return WORKLOADS[name]()
+
+
+def load_observations(name: str, path: Path = OBSERVATIONS_PATH) -> np.ndarray:
+    with open(path) as f:
+        data = json.load(f)
+    return np.array(data[name]["y"], dtype=np.float64)
