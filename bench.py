@@ -1,0 +1,368 @@
+#!/usr/bin/env python3
+"""Benchmark: particle-filter log-likelihoods of many theta on one GB300.
+
+One *step* is one pf_loglik call over the whole gene-expression workload
+(4096 theta x 10 trajectories x 1000 particles x 50 observation times,
+2 species / 4 reactions), inputs resident in HBM.  Reported:
+  value        theta-likelihoods/s (whole job, all ranks),
+  ssa_events_per_s, e2e (through the C ABI with host buffers, copies timed),
+  roofline     FP64 pipe of the filter kernel (the hot kernel),
+  cpu_baseline the oracle on the host cores, on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank evaluates its own theta batch (weak
+scaling, no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_1606_08281_gb300 import workloads as W  # noqa: E402
+
+WORKLOAD = "gene_expression"
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB L2
+# FP64 roofline of the filter kernel.  Nominal GB300 FP64 rate 1.25 TFLOP/s
+# at the 2070 MHz maximum SM clock over 152 SMs = 4 flops per SM per clock.
+FP64_FLOPS_PER_SM_CLK = 4.0
+N_SMS = 152
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_TFLOPS = FP64_FLOPS_PER_SM_CLK * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
+# FP64 flops priced per call of log() and IEEE division (FMA = 2 flops), from
+# ncu FP64 instruction counters on the pf_fp64_probe kernels; None = price
+# them live from the probe's timing relative to the FMA peak.
+FP64_FLOPS_LOG = None
+FP64_FLOPS_DIV = None
+
+
+def flops_per_event(R: int, f_log: float, f_div: float) -> float:
+    """Algorithmic FP64 flops of one direct-method SSA event: R propensity
+    products and R prefix additions, u2*a0, t + tau, one log, one division."""
+    return 2.0 * R + 2.0 + f_log + f_div
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, reasons)."""
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r.split(",") for r in self.file.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ oracle leg
+def _oracle_rows(args):
+    """Worker: oracle on theta rows (in order) until the deadline."""
+    name, rows, deadline = args
+    sys.path.insert(0, str(ROOT))
+    from oracle import pf_oracle
+    w = W.get(name)
+    th = w.thetas()
+    y = w.observations()
+    done, busy, events = 0, 0.0, 0
+    for m in rows:
+        if time.time() >= deadline:
+            break
+        t0 = time.time()
+        r = pf_oracle.pf_loglik(w.net, th[m:m + 1], w.x0, w.obs_times, y, w.C, w.sigma, w.N,
+                                w.filter_seed, theta_ids=[m])
+        dt = time.time() - t0
+        if time.time() > deadline + 60:     # a row that overran far: not counted
+            break
+        done += 1
+        busy += dt
+        events += int(r["events"].sum())
+    return done, busy, events
+
+
+def oracle_baseline(name: str, seconds: float) -> dict:
+    """The oracle as it stands, one process per host core (spawned), each on its
+    own slice of theta rows, for a bounded wall time."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    w = W.get(name)
+    order = np.arange(w.M)
+    slices = [order[i::cores] for i in range(cores)]
+    deadline = time.time() + seconds
+    ctx = mp.get_context("spawn")
+    t0 = time.time()
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_oracle_rows, [(name, list(map(int, s)), deadline) for s in slices])
+    wall = time.time() - t0
+    rows = sum(r[0] for r in res)
+    busy = sum(r[1] for r in res)
+    events = sum(r[2] for r in res)
+    per_core_rate = rows / busy if busy > 0 else 0.0
+    return {
+        "value": per_core_rate * cores,
+        "unit": "theta-likelihoods/s",
+        "cores": cores,
+        "kind": "oracle",
+        "ssa_events_per_s": (events / busy * cores) if busy > 0 else 0.0,
+        "sample": (f"{rows} theta rows (x{w.T} trajectories x {w.N} particles x {w.K} times) of "
+                   f"the {name} batch, taken in row order by {cores} single-threaded oracle "
+                   f"processes within {seconds:.0f} s; rate = rows / busy time, x cores"),
+        "wall_s": wall,
+    }
+
+
+def run_reference(a, rank: int) -> None:
+    if rank != 0:
+        return
+    w = W.get(a.workload)
+    per_step = max(5.0, min(30.0, 150.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        oracle_baseline(a.workload, per_step / 4)
+    vals = []
+    last = None
+    for _ in range(a.steps):
+        last = oracle_baseline(a.workload, per_step)
+        vals.append(last["value"])
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference",
+        "metric": "theta-likelihoods/s", "value": value, "unit": "theta-likelihoods/s",
+        "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * w.M / value if value > 0 else None,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_of(w),
+        "cpu_baseline": {k: last[k] for k in ("kind", "cores", "sample")} | {"value": value,
+                                                                           "unit": last["unit"]},
+        "e2e": {"value": value, "unit": "theta-likelihoods/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "ssa_events_per_s": last["ssa_events_per_s"],
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_of(w) -> dict:
+    return {"workload": f"{w.name}: U={w.U} R={w.R} P={w.P} K={w.K} T={w.T} M={w.M} N={w.N}",
+            "M_theta": w.M, "T_trajectories": w.T, "K_times": w.K, "N_particles": w.N,
+            "species": w.U, "reactions": w.R,
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": "weak: one theta batch per GPU"}
+
+
+# ---------------------------------------------------------------- GPU leg
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    a = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    if a.impl == "reference":
+        run_reference(a, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_1606_08281_gb300 import build, pf
+    if rank == 0:
+        build.build()
+    if world > 1:
+        dist.barrier()
+    pf.load()
+
+    w = W.get(a.workload)
+    th_np = w.thetas() if rank == 0 else W.log_uniform(
+        np.random.default_rng(w.theta_seed + 7919 * rank), w.prior_lo, w.prior_hi, w.M)
+    y_np = w.observations()
+    th = torch.from_numpy(th_np).to(dev)
+    yd = torch.from_numpy(y_np).to(dev)
+    M, T = w.M, w.T
+    out = {"loglik": torch.empty(M, dtype=torch.float64, device=dev),
+           "status": torch.empty(M, dtype=torch.uint8, device=dev),
+           "events": torch.empty((M, T), dtype=torch.int64, device=dev)}
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def step():
+        pf.pf_loglik(w.net, th, w.x0, w.obs_times, yd, w.C, w.sigma, w.N, w.filter_seed,
+                     out=out, stream=stream.cuda_stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev_step = int(out["events"].sum().item())
+    assert int((out["status"] != 0).sum().item()) == 0
+
+    # FP64 cost probe: FMA peak and the price of log / division
+    probe = fp64_probe(pf)
+
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    local_ms = float(np.mean(times))
+    if world > 1:
+        t = torch.tensor([local_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        ms = float(t.item())
+    else:
+        ms = local_ms
+
+    # end to end through the C ABI with host (pinned) buffers
+    th_pin = torch.from_numpy(th_np).pin_memory()
+    y_pin = torch.from_numpy(y_np).pin_memory()
+    ll_pin = torch.empty(M, dtype=torch.float64).pin_memory()
+    st_pin = torch.empty(M, dtype=torch.uint8).pin_memory()
+    host_out = {"loglik": ll_pin.numpy(), "status": st_pin.numpy()}
+    e2e_times = []
+    for _ in range(a.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pf.pf_loglik(w.net, th_pin.numpy(), w.x0, w.obs_times, y_pin.numpy(), w.C, w.sigma, w.N,
+                     w.filter_seed, out=host_out)
+        e2e_times.append(time.perf_counter() - t0)
+    assert np.array_equal(host_out["loglik"], out["loglik"].cpu().numpy()) or rank != 0
+    e2e_s = float(np.mean(e2e_times))
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = oracle_baseline(a.workload, a.cpu_seconds)
+
+    if rank == 0:
+        f_log = FP64_FLOPS_LOG if FP64_FLOPS_LOG is not None else probe["log_fma_equiv_flops"]
+        f_div = FP64_FLOPS_DIV if FP64_FLOPS_DIV is not None else probe["div_fma_equiv_flops"]
+        fpe = flops_per_event(w.R, f_log, f_div)
+        achieved = fpe * ev_step / (local_ms * 1e-3) / 1e12
+        value = world * M / (ms * 1e-3)
+        h2d = th_np.nbytes + y_np.nbytes + w.obs_times.nbytes
+        d2h = M * 8 + M
+        line = {
+            "metric": "theta-likelihoods/s", "value": value, "unit": "theta-likelihoods/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_of(w),
+            "ssa_events_per_s": world * ev_step / (ms * 1e-3),
+            "events_per_step": ev_step,
+            "clocks": clk,
+            "e2e": {"value": world * M / e2e_s, "unit": "theta-likelihoods/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": 2 * a.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
+                         "traffic": None,
+                         "kernel": "filter_kernel (FP64 pipe)",
+                         "flops_per_event": fpe,
+                         "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 4 flops/SM/clk x "
+                                        "152 SMs x 2070 MHz",
+                         "kernel_ms": local_ms},
+            "fp64_probe": probe,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def fp64_probe(pf) -> dict:
+    blocks, threads = 152 * 4, 256
+    res = {}
+    iters = {0: 4096, 1: 256, 2: 512}
+    for kind in (0, 1, 2):
+        pf.pf_fp64_probe(kind, blocks, threads, 16)          # warm-up
+        ms, _ = pf.pf_fp64_probe(kind, blocks, threads, iters[kind])
+        res[kind] = ms
+    ops = blocks * threads * 8
+    fma_rate = ops * iters[0] / (res[0] * 1e-3)            # FMA instructions per second
+    log_rate = ops * iters[1] / (res[1] * 1e-3)            # log calls (+2 adds) per second
+    div_rate = ops * iters[2] / (res[2] * 1e-3)
+    return {
+        "fma_tflops": 2 * fma_rate / 1e12,
+        "log_per_s": log_rate, "div_per_s": div_rate,
+        # cost of one call in FMA-equivalent flops (2 per FMA), minus its two adds
+        "log_fma_equiv_flops": 2 * fma_rate / log_rate - 2.0,
+        "div_fma_equiv_flops": 2 * fma_rate / div_rate - 2.0,
+    }
+
+
+if __name__ == "__main__":
+    main()

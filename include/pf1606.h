@@ -1,0 +1,184 @@
+/*
+ * pf1606.h -- C ABI of the GB300 particle-filter likelihood library.
+ *
+ * The library evaluates, for M candidate parameter vectors theta at once, the
+ * trajectory-data log-likelihood log p(y | theta) of a stochastic chemical
+ * reaction network, each estimated by a bootstrap particle filter whose
+ * particles are propagated between observation times by Gillespie's stochastic
+ * simulation algorithm (direct method), weighted by the Gaussian measurement
+ * density of y(t_k) given C x(t_k), and resampled systematically.
+ * (Mikelson & Khammash, arXiv 1606.08281: network model, Sec. "Chemical
+ * Reaction Networks"; observation model, Sec. "General Task"; filter,
+ * Supp. I, algorithm "Likelihood Approximation using particle filter" and
+ * Eq. (likelihood approx.); product over trajectories, Supp. I.)
+ *
+ * Symbols: U species, R reactions, d = number of theta columns, K observation
+ * times, T observed trajectories, P observed dimensions, N particles per
+ * filter, M theta rows.  One *filter* is one (theta row, trajectory) pair.
+ *
+ * Conventions
+ *   - Every array is dense and row-major (C order).
+ *   - Errors are negative return codes, never aborts; pf_last_error() returns a
+ *     human-readable detail for the calling thread.  Outputs are written only
+ *     when the call returns PF_OK.
+ *   - A numerical failure of one theta does not fail the call: it is reported
+ *     in status[m] and loglik[m] is -inf (PF_ST_BUDGET, PF_ST_NONFINITE) or
+ *     NaN (PF_ST_INVALID_THETA).
+ *   - Each result depends only on (problem, theta row, its row index m within
+ *     the call, N, seed, event budget), never on the other rows of the batch.
+ *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
+ *     counter = (draw j, particle i, (trajectory << 20) | interval k, row m);
+ *     hence K < 2^20 and T < 2^12.
+ *   - No function keeps a caller pointer after it returns.
+ */
+#ifndef PF1606_H
+#define PF1606_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return codes ---------------------------------------------------- */
+#define PF_OK 0
+#define PF_EINVAL (-1)    /* an argument is out of range or malformed        */
+#define PF_ENOMEM (-2)    /* device or host memory could not be obtained     */
+#define PF_ECUDA (-3)     /* a CUDA runtime call failed (detail in last_error)*/
+#define PF_ETIMEOUT (-4)  /* a bounded device wait expired                   */
+#define PF_EAGAIN (-5)    /* request not finished yet (pf_poll)              */
+#define PF_ENOTFOUND (-6) /* unknown request / problem id                     */
+#define PF_EBUSY (-7)     /* admission refused: not enough budgeted memory   */
+
+/* ---- per-theta status codes (status[m]) -------------------------------- */
+#define PF_ST_OK 0
+#define PF_ST_BUDGET 1        /* a particle needed more than event_budget draws
+                                 in one interval; loglik = -inf              */
+#define PF_ST_NONFINITE 2     /* a weight was not finite; loglik = -inf       */
+#define PF_ST_INVALID_THETA 3 /* theta row has a negative or non-finite entry;
+                                 loglik = NaN, nothing was simulated          */
+
+/* ---- limits ------------------------------------------------------------ */
+#define PF_MAX_SPECIES 16
+#define PF_MAX_REACTIONS 32
+#define PF_MAX_OBS_DIM 8
+#define PF_MAX_PARTICLES 16384
+#define PF_DEFAULT_EVENT_BUDGET (1ull << 20)
+
+/*
+ * Reaction network (Sec. "Chemical Reaction Networks"): reaction r consumes
+ * reactants[r][u] = p_ru and produces products[r][u] = q_ru molecules of
+ * species u.  Its propensity is mass action in Gillespie's combinatorial form,
+ *     a_r(x) = theta[rate_index[r]] * prod_u binom(x_u, p_ru),
+ * with total order sum_u p_ru <= 2.  rate_index may be NULL (then column r,
+ * and d >= R is required).  All pointers are HOST pointers.
+ */
+typedef struct {
+    int32_t n_species;          /* U, 1..PF_MAX_SPECIES     */
+    int32_t n_reactions;        /* R, 1..PF_MAX_REACTIONS   */
+    const int32_t *reactants;   /* [R][U], 0..2             */
+    const int32_t *products;    /* [R][U], 0..127           */
+    const int32_t *rate_index;  /* [R] in 0..d-1, or NULL   */
+} pf_network;
+
+/*
+ * Options (pass NULL for defaults).
+ *   event_budget  max draws per particle per interval (0 = default 2^20).
+ *   device_ptrs   0: thetas, y, loglik, status and the diagnostic arrays are
+ *                 HOST pointers; the call copies, computes and returns when
+ *                 the results are on the host.
+ *                 1: they are DEVICE pointers on the current device; the call
+ *                 validates on the host, enqueues the work on `stream` and
+ *                 returns; the results are ready when the stream reaches that
+ *                 point.  The network, x0, obs_times, C and sigma are always
+ *                 host arrays (small; copied by the call).
+ *   stream        cudaStream_t to use (NULL = the legacy default stream).
+ *   block_threads threads per filter block (0 = library choice; else a
+ *                 multiple of 32 in 32..256).
+ *   ll_traj       optional [M][T] per-filter log-likelihood (-inf when the
+ *                 filter failed).
+ *   events        optional [M][T] number of reactions fired per filter.
+ *   digest        optional [M][T] sum over intervals k and particle slots j of
+ *                 a 64-bit mix of (k, j, ancestor of j, state of j after the
+ *                 simulation step), modulo 2^64: a fingerprint of the whole
+ *                 resampling / simulation history, used to compare paths.
+ *   final_states  optional [M][T][N][U] particle states after the last
+ *                 interval (int32).
+ *   Diagnostics are defined only for filters whose status is PF_ST_OK.
+ */
+typedef struct {
+    uint64_t event_budget;
+    int32_t device_ptrs;
+    int32_t block_threads;
+    void *stream;
+    double *ll_traj;
+    uint64_t *events;
+    uint64_t *digest;
+    int32_t *final_states;
+} pf_options;
+
+/*
+ * pf_loglik -- log-likelihood of M theta rows (Supp. I: filter per
+ * trajectory, product over trajectories).
+ *
+ *   thetas     [M][d] rate constants (>= 0, finite; others get
+ *              PF_ST_INVALID_THETA).
+ *   x0         [U] initial counts (>= 0), identical for every particle
+ *              (Supp. I: "H states X_0 sampled from some initial
+ *              distribution", here a point mass).
+ *   obs_times  [K] strictly increasing, obs_times[0] >= 0.  Particles start
+ *              at time 0; the first step simulates 0 -> obs_times[0].
+ *   y          [T][K][P] observations.
+ *   C          [P][U] observation matrix; sigma [P] > 0 noise std. devs:
+ *              y_k ~ N(C x(t_k), diag(sigma^2)).
+ *   n_particles N in 1..PF_MAX_PARTICLES.
+ *   seed       Philox key.
+ *   loglik     [M] out: sum over trajectories of the filter estimate
+ *              log p_hat(y^traj | theta), trajectories added in order.
+ *   status     [M] out (may be NULL).
+ * Returns PF_OK or a negative code.  M = 0 is valid and does nothing.
+ */
+int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
+              const int32_t *x0, const double *obs_times, int32_t K, const double *y,
+              int32_t T, int32_t P, const double *C, const double *sigma, int32_t n_particles,
+              uint64_t seed, double *loglik, uint8_t *status, const pf_options *opt);
+
+/* Text for a return code (static storage). */
+const char *pf_strerror(int code);
+
+/* Detail of the last error on the calling thread ("" if none). */
+const char *pf_last_error(void);
+
+/* Library version string. */
+const char *pf_version(void);
+
+/*
+ * pf_philox4x32_10 -- n Philox4x32-10 blocks computed on the device, for
+ * checking the device generator against known answers.  ctr [n][4],
+ * key [n][2], out [n][4]; host pointers.  Published definition: Salmon et al.,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC'11.
+ */
+int pf_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n);
+
+/*
+ * pf_fp64_probe -- measurement support, with no counterpart in the paper.
+ * Runs blocks x threads threads, each iterating `iters` times over eight
+ * independent chains of one FP64 operation kind, and returns the device time
+ * in milliseconds (CUDA events) and a checksum (may be NULL).
+ *   kind 0: fused multiply-add (the FP64 pipe's peak rate: 16 flops per
+ *           iteration and thread);
+ *   kind 1: log() plus two additions per chain step;
+ *   kind 2: IEEE division plus two additions per chain step.
+ * With ncu's FP64 instruction counters this prices one log() and one division
+ * in FP64 operations, the per-event cost model of the SSA kernel's roofline.
+ * Returns PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.  Allocates and frees its
+ * own output buffer; synchronous.
+ */
+int pf_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters,
+                  double *elapsed_ms, double *checksum);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PF1606_H */

@@ -1,0 +1,263 @@
+// C ABI of the particle-filter likelihood library: validation, device
+// buffers, copies and launches.  The arithmetic of the method lives in the
+// kernels (pf_filter.cu); this layer only checks arguments, lays the network
+// out in the kernels' tables and moves data.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "pf1606.h"
+#include "pf_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    if (e == cudaErrorMemoryAllocation) return fail(PF_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+    return fail(PF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define PF_CUDA(call, what)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);    \
+    } while (0)
+
+// Build the kernels' network tables from the caller's description.
+int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P, const double *C,
+                 const double *sigma, pf::NetTables &t) {
+    if (!net || !net->reactants || !net->products) return fail(PF_EINVAL, "network is NULL");
+    const int U = net->n_species, R = net->n_reactions;
+    if (U < 1 || U > PF_MAX_SPECIES) return fail(PF_EINVAL, "n_species %d outside 1..%d", U, PF_MAX_SPECIES);
+    if (R < 1 || R > PF_MAX_REACTIONS) return fail(PF_EINVAL, "n_reactions %d outside 1..%d", R, PF_MAX_REACTIONS);
+    if (P < 1 || P > PF_MAX_OBS_DIM) return fail(PF_EINVAL, "P %d outside 1..%d", P, PF_MAX_OBS_DIM);
+    if (d < 1) return fail(PF_EINVAL, "d must be >= 1");
+    if (!net->rate_index && d < R) return fail(PF_EINVAL, "rate_index is NULL but d (%d) < R (%d)", d, R);
+    if (!x0 || !C || !sigma) return fail(PF_EINVAL, "x0, C and sigma are required");
+    memset(&t, 0, sizeof(t));
+    t.U = U; t.R = R; t.P = P; t.d = d;
+    for (int r = 0; r < R; ++r) {
+        const int col = net->rate_index ? net->rate_index[r] : r;
+        if (col < 0 || col >= d) return fail(PF_EINVAL, "rate_index[%d] = %d outside 0..%d", r, col, d - 1);
+        t.rate_col[r] = col;
+        t.sp_a[r] = t.sp_b[r] = -1;
+        t.ord_a[r] = t.ord_b[r] = 0;
+        int order = 0;
+        for (int u = 0; u < U; ++u) {
+            const int p = net->reactants[r * U + u], q = net->products[r * U + u];
+            if (p < 0 || q < 0) return fail(PF_EINVAL, "negative stoichiometry in reaction %d", r);
+            if (q > 127) return fail(PF_EINVAL, "product count %d > 127 in reaction %d", q, r);
+            order += p;
+            if (order > 2) return fail(PF_EINVAL, "reaction %d has total order > 2", r);
+            if (p > 0) {
+                if (t.sp_a[r] < 0) { t.sp_a[r] = (int8_t)u; t.ord_a[r] = (int8_t)p; }
+                else { t.sp_b[r] = (int8_t)u; t.ord_b[r] = (int8_t)p; }
+            }
+            const int delta = q - p;
+            if (delta != 0) {
+                t.ch_sp[r][t.n_change[r]] = (int8_t)u;
+                t.ch_delta[r][t.n_change[r]] = (int16_t)delta;
+                t.n_change[r]++;
+            }
+        }
+    }
+    // dependency masks: r' must be recomputed after r when r changes a reactant of r'
+    for (int r = 0; r < R; ++r) {
+        uint32_t mask = 0;
+        for (int i = 0; i < t.n_change[r]; ++i) {
+            const int u = t.ch_sp[r][i];
+            for (int r2 = 0; r2 < R; ++r2)
+                if (net->reactants[r2 * U + u] > 0) mask |= 1u << r2;
+        }
+        t.dep[r] = mask;
+    }
+    for (int u = 0; u < U; ++u) {
+        if (x0[u] < 0) return fail(PF_EINVAL, "x0[%d] = %d < 0", u, x0[u]);
+        t.x0[u] = x0[u];
+    }
+    for (int p = 0; p < P; ++p) {
+        if (!(std::isfinite(sigma[p]) && sigma[p] > 0.0)) return fail(PF_EINVAL, "sigma[%d] must be finite and > 0", p);
+        t.sigma[p] = sigma[p];
+        for (int u = 0; u < U; ++u) {
+            if (!std::isfinite(C[p * U + u])) return fail(PF_EINVAL, "C[%d][%d] is not finite", p, u);
+            t.C[p][u] = C[p * U + u];
+        }
+    }
+    return PF_OK;
+}
+
+// int32 counts stay in range if every interval stays within the budget.
+int check_count_range(const pf::NetTables &t, int K, uint64_t budget) {
+    int max_gain = 0, x0max = 0;
+    for (int r = 0; r < t.R; ++r)
+        for (int i = 0; i < t.n_change[r]; ++i) max_gain = std::max<int>(max_gain, t.ch_delta[r][i]);
+    for (int u = 0; u < t.U; ++u) x0max = std::max(x0max, t.x0[u]);
+    const double worst = (double)x0max + (double)K * (double)budget * (double)max_gain;
+    if (worst >= 2147483647.0)
+        return fail(PF_EINVAL, "x0 + K * event_budget * max gain (%.3g) could overflow int32 counts; lower event_budget", worst);
+    return PF_OK;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    cudaStream_t s = nullptr;
+    ~DevBuf() { if (p) cudaFreeAsync(p, s); }
+    cudaError_t alloc(size_t bytes, cudaStream_t st) {
+        s = st;
+        return bytes ? cudaMallocAsync(&p, bytes, st) : cudaSuccess;
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+const char *pf_strerror(int code) {
+    switch (code) {
+        case PF_OK: return "ok";
+        case PF_EINVAL: return "invalid argument";
+        case PF_ENOMEM: return "out of memory";
+        case PF_ECUDA: return "CUDA runtime error";
+        case PF_ETIMEOUT: return "bounded device wait expired";
+        case PF_EAGAIN: return "not finished yet";
+        case PF_ENOTFOUND: return "unknown id";
+        case PF_EBUSY: return "admission refused: memory budget";
+        default: return "unknown error code";
+    }
+}
+
+const char *pf_last_error(void) { return g_last_error.c_str(); }
+
+const char *pf_version(void) { return "pf1606 0.1 (sm_103a)"; }
+
+int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
+              const int32_t *x0, const double *obs_times, int32_t K, const double *y, int32_t T,
+              int32_t P, const double *C, const double *sigma, int32_t n_particles,
+              uint64_t seed, double *loglik, uint8_t *status, const pf_options *opt) {
+    g_last_error.clear();
+    pf_options o{};
+    if (opt) o = *opt;
+    const uint64_t budget = o.event_budget ? o.event_budget : PF_DEFAULT_EVENT_BUDGET;
+    const int N = n_particles;
+    if (M < 0) return fail(PF_EINVAL, "M < 0");
+    if (K < 1 || K >= (1 << 20)) return fail(PF_EINVAL, "K %d outside 1..2^20-1", K);
+    if (T < 1 || T >= 4096) return fail(PF_EINVAL, "T %d outside 1..4095", T);
+    if (N < 1 || N > PF_MAX_PARTICLES) return fail(PF_EINVAL, "n_particles %d outside 1..%d", N, PF_MAX_PARTICLES);
+    if (budget > 0xFFFFFFFFull) return fail(PF_EINVAL, "event_budget must be < 2^32");
+    if (!obs_times) return fail(PF_EINVAL, "obs_times is NULL");
+    if (M > 0 && (!thetas || !y || !loglik)) return fail(PF_EINVAL, "NULL array argument");
+    if (M > 0xFFFFFFFFll) return fail(PF_EINVAL, "M must be < 2^32");
+    if (M * (int64_t)T > 0x7FFFFFFFll) return fail(PF_EINVAL, "M * T must be < 2^31");
+    pf::FilterArgs a{};
+    int rc = build_tables(net, d, x0, P, C, sigma, a.net);
+    if (rc) return rc;
+    rc = check_count_range(a.net, K, budget);
+    if (rc) return rc;
+    int B = o.block_threads;
+    if (B == 0) B = std::min(256, ((N + 31) / 32) * 32);
+    if (B < 32 || B > 256 || (B % 32)) return fail(PF_EINVAL, "block_threads %d must be a multiple of 32 in 32..256", B);
+    const size_t smem = pf::filter_smem_bytes(N, a.net.U, B);
+    int dev = 0, smem_max = 0;
+    PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    PF_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
+    if (smem + sizeof(pf::NetTables) + 2048 > (size_t)smem_max)
+        return fail(PF_EINVAL, "N=%d with U=%d needs %zu bytes of shared memory per filter (limit %d)", N, a.net.U, smem, smem_max);
+
+    cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+    // observation times (always a host array): strictly increasing, >= 0, finite
+    for (int k = 0; k < K; ++k) {
+        const bool bad = !std::isfinite(obs_times[k]) ||
+                         (k == 0 ? obs_times[k] < 0.0 : !(obs_times[k] > obs_times[k - 1]));
+        if (bad) return fail(PF_EINVAL, "obs_times must be finite, >= 0 and strictly increasing (index %d)", k);
+    }
+    if (M == 0) return PF_OK;
+
+    const int64_t F = M * T;
+    a.M = M; a.K = K; a.T = T; a.N = N;
+    a.seed = seed;
+    a.budget = budget;
+    DevBuf b_theta, b_times, b_y, b_ll, b_st, b_llf, b_stf, b_evf, b_dgf, b_fs;
+    const size_t n_th = sizeof(double) * (size_t)M * d, n_y = sizeof(double) * (size_t)T * K * P;
+    const size_t n_fs = sizeof(int32_t) * (size_t)F * N * a.net.U;
+    double *d_ll = loglik;
+    uint8_t *d_st = status;
+    PF_CUDA(b_times.alloc(sizeof(double) * K, s), "alloc obs_times");
+    PF_CUDA(cudaMemcpyAsync(b_times.p, obs_times, sizeof(double) * K, cudaMemcpyHostToDevice, s), "copy obs_times");
+    a.obs_times = (const double *)b_times.p;
+    if (o.device_ptrs) {
+        a.thetas = thetas; a.y = y;
+    } else {
+        PF_CUDA(b_theta.alloc(n_th, s), "alloc thetas");
+        PF_CUDA(b_y.alloc(n_y, s), "alloc y");
+        PF_CUDA(b_ll.alloc(sizeof(double) * M, s), "alloc loglik");
+        PF_CUDA(b_st.alloc(M, s), "alloc status");
+        PF_CUDA(cudaMemcpyAsync(b_theta.p, thetas, n_th, cudaMemcpyHostToDevice, s), "copy thetas");
+        PF_CUDA(cudaMemcpyAsync(b_y.p, y, n_y, cudaMemcpyHostToDevice, s), "copy y");
+        a.thetas = (const double *)b_theta.p; a.y = (const double *)b_y.p;
+        d_ll = (double *)b_ll.p;
+        d_st = (uint8_t *)b_st.p;
+    }
+    // per-filter results: the caller's arrays if given and on the device, else scratch
+    auto pick = [&](void *user, DevBuf &buf, size_t bytes, void **out) -> cudaError_t {
+        if (user && o.device_ptrs) { *out = user; return cudaSuccess; }
+        cudaError_t e = buf.alloc(bytes, s);
+        *out = buf.p;
+        return e;
+    };
+    void *p;
+    PF_CUDA(pick(o.ll_traj, b_llf, sizeof(double) * F, &p), "alloc ll_traj"); a.ll_f = (double *)p;
+    PF_CUDA(pick(nullptr, b_stf, F, &p), "alloc status_traj"); a.st_f = (uint8_t *)p;
+    PF_CUDA(pick(o.events, b_evf, sizeof(uint64_t) * F, &p), "alloc events"); a.ev_f = (uint64_t *)p;
+    if (o.digest) { PF_CUDA(pick(o.digest, b_dgf, sizeof(uint64_t) * F, &p), "alloc digest"); a.dg_f = (uint64_t *)p; }
+    if (o.final_states) { PF_CUDA(pick(o.final_states, b_fs, n_fs, &p), "alloc final_states"); a.final_states = (int32_t *)p; }
+
+    int e = pf::launch_filter(a, B, d_ll, d_st, s);
+    if (e) return cuda_fail((cudaError_t)e, "filter launch");
+
+    if (!o.device_ptrs) {
+        PF_CUDA(cudaMemcpyAsync(loglik, d_ll, sizeof(double) * M, cudaMemcpyDeviceToHost, s), "copy loglik");
+        if (status) PF_CUDA(cudaMemcpyAsync(status, d_st, M, cudaMemcpyDeviceToHost, s), "copy status");
+        if (o.ll_traj) PF_CUDA(cudaMemcpyAsync(o.ll_traj, a.ll_f, sizeof(double) * F, cudaMemcpyDeviceToHost, s), "copy ll_traj");
+        if (o.events) PF_CUDA(cudaMemcpyAsync(o.events, a.ev_f, sizeof(uint64_t) * F, cudaMemcpyDeviceToHost, s), "copy events");
+        if (o.digest) PF_CUDA(cudaMemcpyAsync(o.digest, a.dg_f, sizeof(uint64_t) * F, cudaMemcpyDeviceToHost, s), "copy digest");
+        if (o.final_states) PF_CUDA(cudaMemcpyAsync(o.final_states, a.final_states, n_fs, cudaMemcpyDeviceToHost, s), "copy final_states");
+        PF_CUDA(cudaStreamSynchronize(s), "synchronize");
+    }
+    return PF_OK;
+}
+
+int pf_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n) {
+    g_last_error.clear();
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) return fail(PF_EINVAL, "bad arguments");
+    if (n == 0) return PF_OK;
+    cudaStream_t s = nullptr;
+    DevBuf bc, bk, bo;
+    PF_CUDA(bc.alloc(16 * (size_t)n, s), "alloc");
+    PF_CUDA(bk.alloc(8 * (size_t)n, s), "alloc");
+    PF_CUDA(bo.alloc(16 * (size_t)n, s), "alloc");
+    PF_CUDA(cudaMemcpyAsync(bc.p, ctr, 16 * (size_t)n, cudaMemcpyHostToDevice, s), "copy");
+    PF_CUDA(cudaMemcpyAsync(bk.p, key, 8 * (size_t)n, cudaMemcpyHostToDevice, s), "copy");
+    int e = pf::launch_philox((const uint32_t *)bc.p, (const uint32_t *)bk.p, (uint32_t *)bo.p, n, s);
+    if (e) return cuda_fail((cudaError_t)e, "philox launch");
+    PF_CUDA(cudaMemcpyAsync(out, bo.p, 16 * (size_t)n, cudaMemcpyDeviceToHost, s), "copy");
+    PF_CUDA(cudaStreamSynchronize(s), "synchronize");
+    return PF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,462 @@
+// Particle-filter kernels for sm_103a.
+//
+// One thread block runs one filter, i.e. one (theta row, observed trajectory)
+// pair, through all K observation times (Supp. I, algorithm "Likelihood
+// Approximation using particle filter"):
+//   resample by the previous weights -> simulate every particle to t_k with
+//   the direct-method SSA -> Gaussian weight -> log-sum-exp increment.
+// The whole particle population lives in shared memory: states int32 [U][N]
+// (two buffers for the gather), the weights / integer-weight prefix sums
+// (8 bytes per particle, reused), and the ancestor indices.  Nothing of the
+// filter touches HBM between its first load and its final store.
+//
+// Arithmetic that decides integer outcomes (propensities, their prefix sums,
+// event times, the Gaussian exponent) uses explicit round-to-nearest
+// intrinsics so that the compiler cannot fuse a multiply and an add; the
+// results then match a plain sequential FP64 restatement bit for bit, except
+// where CUDA's log/exp differ from another libm in the last place.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "pf_internal.h"
+#include "philox.cuh"
+
+namespace pf {
+namespace {
+
+constexpr int kMaxWarps = 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kResampleLane = 0xFFFFFFFFu;
+
+struct SharedHead {
+    NetTables net;
+    double rate[PF_MAX_REACTIONS];   // theta[rate_col[r]] of this filter's row
+    double red_d[kMaxWarps];
+    unsigned long long red_u[kMaxWarps];
+    double bcast_d;
+    unsigned long long u_off;
+    double ll;
+    double lognorm;
+    int status;
+    int valid;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ long long binom_small(int x, int p) {
+    const long long xl = x;
+    if (p == 0) return 1;
+    if (p == 1) return xl;
+    return x >= 2 ? (xl * (xl - 1)) / 2 : 0;  // p == 2
+}
+
+// a_r = theta_rho(r) * prod_u binom(x_u, p_ru)  (Sec. "Chemical Reaction Networks")
+__device__ __forceinline__ double propensity(int r, const SharedHead &sh, const int *xs, int Np,
+                                             int j) {
+    const NetTables &n = sh.net;
+    long long h = 1;
+    const int sa = n.sp_a[r];
+    if (sa >= 0) h = binom_small(xs[sa * Np + j], n.ord_a[r]);
+    const int sb = n.sp_b[r];
+    if (sb >= 0) h *= binom_small(xs[sb * Np + j], n.ord_b[r]);
+    return __dmul_rn(sh.rate[r], __ll2double_rn(h));
+}
+
+template <int RM>
+__device__ __forceinline__ double prefix_sums(const double (&a)[RM], double (&S)[RM], int R) {
+    double run = a[0];
+    S[0] = run;
+#pragma unroll
+    for (int r = 1; r < RM; ++r) {
+        if (r < R) run = __dadd_rn(run, a[r]);
+        S[r] = run;
+    }
+    return run;
+}
+
+// Advance particle slot j from t to t_end by Gillespie's direct method.
+// Returns PF_ST_OK or PF_ST_BUDGET; `fired` counts reactions that fired.
+template <int RM>
+__device__ int ssa_advance(const SharedHead &sh, int *xs, int Np, int j, double t, double t_end,
+                           uint32_t key0, uint32_t key1, uint32_t lane, uint32_t mrow,
+                           uint64_t budget, unsigned long long &fired) {
+    const int R = sh.net.R;
+    double a[RM], S[RM];
+#pragma unroll
+    for (int r = 0; r < RM; ++r) a[r] = (r < R) ? propensity(r, sh, xs, Np, j) : 0.0;
+    double a0 = prefix_sums<RM>(a, S, R);
+    uint64_t draws = 0;
+    for (;;) {
+        if (!(a0 > 0.0)) return PF_ST_OK;  // absorbing state
+        if (draws >= budget) return PF_ST_BUDGET;
+        const Philox4 w = philox4x32_10(static_cast<uint32_t>(draws), static_cast<uint32_t>(j),
+                                        lane, mrow, key0, key1);
+        ++draws;
+        const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+        const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
+        const double u1 = scaled_u53((r0 >> 11) + 1ull);        // (0, 1]
+        const uint64_t v2 = r1 >> 11;
+        const double u2 = v2 ? scaled_u53(v2) : 0.0;            // [0, 1)
+        const double tau = __ddiv_rn(-log(u1), a0);
+        const double t_next = __dadd_rn(t, tau);
+        if (t_next > t_end) return PF_ST_OK;  // pending event lies past t_end: discard
+        const double target = __dmul_rn(u2, a0);
+        int chosen = 0;
+#pragma unroll
+        for (int r = 0; r < RM; ++r) chosen += (r < R && S[r] <= target) ? 1 : 0;
+        if (chosen >= R) {  // rounding guard: last reaction that can fire
+            chosen = 0;
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+                if (r < R && a[r] > 0.0) chosen = r;
+        }
+        const int nch = sh.net.n_change[chosen];
+        for (int i = 0; i < nch; ++i)
+            xs[sh.net.ch_sp[chosen][i] * Np + j] += sh.net.ch_delta[chosen][i];
+        t = t_next;
+        ++fired;
+        const uint32_t deps = sh.net.dep[chosen];
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+            if ((deps >> r) & 1u) a[r] = propensity(r, sh, xs, Np, j);
+        a0 = prefix_sums<RM>(a, S, R);
+    }
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+// Fingerprint of slot j after the simulation step of interval k.
+__device__ __forceinline__ uint64_t slot_digest(uint32_t k, uint32_t j, uint32_t anc,
+                                                const int *xs, int Np, int U) {
+    uint64_t h = mix64((static_cast<uint64_t>(k) << 32) | j);
+    h = mix64(h ^ static_cast<uint64_t>(anc));
+    for (int u = 0; u < U; ++u) h = mix64(h ^ static_cast<uint64_t>(static_cast<uint32_t>(xs[u * Np + j])));
+    return h;
+}
+
+// Block-wide reductions (every thread receives the result).
+__device__ __forceinline__ double block_max(double v, SharedHead &sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.red_d[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < nw ? sh.red_d[lane] : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(kFull, x, o));
+        if (lane == 0) sh.bcast_d = x;
+    }
+    __syncthreads();
+    return sh.bcast_d;
+}
+
+__device__ __forceinline__ double block_sum(double v, SharedHead &sh) {
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.red_d[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < nw ? sh.red_d[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) x = __dadd_rn(x, __shfl_xor_sync(kFull, x, o));
+        if (lane == 0) sh.bcast_d = x;
+    }
+    __syncthreads();
+    return sh.bcast_d;
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, SharedHead &sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.red_u[warp] = v;
+    __syncthreads();
+    unsigned long long x = 0;
+    for (int i = 0; i < nw; ++i) x += sh.red_u[i];
+    return x;
+}
+
+// Inclusive prefix sum of q[0..N) in place (thread t owns a contiguous chunk).
+__device__ void block_scan_u64(unsigned long long *q, int N, SharedHead &sh) {
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = B >> 5;
+    const int chunk = (N + B - 1) / B;
+    const int beg = min(N, tid * chunk), end = min(N, beg + chunk);
+    unsigned long long run = 0;
+    for (int i = beg; i < end; ++i) {
+        run += q[i];
+        q[i] = run;
+    }
+    unsigned long long v = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long n = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += n;
+    }
+    __syncthreads();
+    if (lane == 31) sh.red_u[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long x = lane < nw ? sh.red_u[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long n = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += n;
+        }
+        if (lane < nw) sh.red_u[lane] = x;
+    }
+    __syncthreads();
+    const unsigned long long off = (v - run) + (warp > 0 ? sh.red_u[warp - 1] : 0ull);
+    for (int i = beg; i < end; ++i) q[i] += off;
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ kernels
+template <int RM>
+__global__ void __launch_bounds__(256, 1) filter_kernel(const FilterArgs args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SharedHead sh;
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int T = args.T, N = args.N, K = args.K;
+    const int64_t f = blockIdx.x;
+    const int64_t mrow = f / T;
+    const int traj = static_cast<int>(f - mrow * T);
+
+    {  // network tables -> shared memory
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&args.net);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sh.net);
+        for (int i = tid; i < static_cast<int>(sizeof(NetTables) / 4); i += B) dst[i] = src[i];
+    }
+    const int d = args.net.d, R = args.net.R, U = args.net.U, P = args.net.P;
+    const double *theta = args.thetas + mrow * d;
+    if (tid == 0) {
+        int ok = 1;
+        for (int c = 0; c < d; ++c) {
+            const double v = theta[c];
+            if (!(isfinite(v) && v >= 0.0)) ok = 0;
+        }
+        sh.valid = ok;
+        sh.status = PF_ST_OK;
+        sh.ll = 0.0;
+        double ln = 0.0;
+        for (int p = 0; p < P; ++p) ln = __dadd_rn(ln, log(args.net.sigma[p]));
+        sh.lognorm = __dadd_rn(ln, __dmul_rn(0.5 * static_cast<double>(P), log(2.0 * M_PI)));
+    }
+    if (tid < R) sh.rate[tid] = theta[args.net.rate_col[tid]];
+    __syncthreads();
+    if (!sh.valid) {
+        if (tid == 0) {
+            args.ll_f[f] = __longlong_as_double(0x7FF8000000000000ll);
+            args.st_f[f] = PF_ST_INVALID_THETA;
+            args.ev_f[f] = 0;
+            if (args.dg_f) args.dg_f[f] = 0;
+        }
+        return;
+    }
+
+    const int Np = N;
+    double *wbuf = reinterpret_cast<double *>(smem);                  // [N] weights / q / Q
+    unsigned long long *qbuf = reinterpret_cast<unsigned long long *>(smem);
+    int *xs = reinterpret_cast<int *>(wbuf + N);                       // [U][N]
+    int *xn = xs + U * Np;                                             // [U][N]
+    int *anc = xn + U * Np;                                            // [N]
+
+    for (int j = tid; j < N; j += B)
+        for (int u = 0; u < U; ++u) xs[u * Np + j] = sh.net.x0[u];
+    __syncthreads();
+
+    const uint32_t key0 = static_cast<uint32_t>(args.seed);
+    const uint32_t key1 = static_cast<uint32_t>(args.seed >> 32);
+    const uint32_t m32 = static_cast<uint32_t>(mrow);
+    unsigned long long fired = 0, dig = 0;
+    double t_prev = 0.0;
+
+    for (int k = 0; k < K; ++k) {
+        const uint32_t lane = (static_cast<uint32_t>(traj) << 20) | static_cast<uint32_t>(k);
+        if (k > 0) {
+            // systematic resampling on the integer weights of interval k-1
+            block_scan_u64(qbuf, N, sh);
+            if (tid == 0) {
+                const unsigned long long W = qbuf[N - 1];
+                const Philox4 w = philox4x32_10(0u, kResampleLane, lane, m32, key0, key1);
+                const unsigned long long r64 = (static_cast<unsigned long long>(w.w1) << 32) | w.w0;
+                sh.u_off = __umul64hi(r64, W);
+            }
+            __syncthreads();
+            const unsigned long long W = qbuf[N - 1], u_off = sh.u_off;
+            const unsigned long long Nl = static_cast<unsigned long long>(N);
+            for (int j = tid; j < N; j += B) {
+                const unsigned long long point = u_off + static_cast<unsigned long long>(j) * W;
+                int lo = 0, hi = N - 1;  // a_j = min{i : N Q_i > point}
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (Nl * qbuf[mid] > point) hi = mid; else lo = mid + 1;
+                }
+                anc[j] = lo;
+                for (int u = 0; u < U; ++u) xn[u * Np + j] = xs[u * Np + lo];
+            }
+            __syncthreads();
+            int *tmp = xs; xs = xn; xn = tmp;
+        } else {
+            for (int j = tid; j < N; j += B) anc[j] = j;
+        }
+
+        const double t_k = args.obs_times[k];
+        if (t_k > t_prev) {
+            for (int j = tid; j < N; j += B) {
+                const int st = ssa_advance<RM>(sh, xs, Np, j, t_prev, t_k, key0, key1, lane, m32,
+                                               args.budget, fired);
+                if (st != PF_ST_OK) sh.status = st;
+            }
+        }
+        __syncthreads();
+        if (sh.status != PF_ST_OK) break;
+
+        if (args.dg_f)
+            for (int j = tid; j < N; j += B)
+                dig += slot_digest(static_cast<uint32_t>(k), static_cast<uint32_t>(j),
+                                   static_cast<uint32_t>(anc[j]), xs, Np, U);
+
+        // Gaussian log-weight exponent e_j = -1/2 sum_p ((y_p - (C x_j)_p) / sigma_p)^2
+        const double *yk = args.y + (static_cast<int64_t>(traj) * K + k) * P;
+        double lmax = -INFINITY;
+        for (int j = tid; j < N; j += B) {
+            double acc = 0.0;
+            for (int p = 0; p < P; ++p) {
+                double mu = 0.0;
+                for (int u = 0; u < U; ++u)
+                    mu = __dadd_rn(mu, __dmul_rn(sh.net.C[p][u], static_cast<double>(xs[u * Np + j])));
+                const double z = __ddiv_rn(__dsub_rn(yk[p], mu), sh.net.sigma[p]);
+                acc = __dadd_rn(acc, __dmul_rn(z, z));
+            }
+            const double e = __dmul_rn(-0.5, acc);
+            wbuf[j] = e;
+            lmax = fmax(lmax, e);
+        }
+        const double emax = block_max(lmax, sh);
+        if (!isfinite(emax)) {
+            if (tid == 0) sh.status = PF_ST_NONFINITE;
+            break;
+        }
+        // p(y_k | y_<k) ~ (1/N) sum_j l_j  (Eq. likelihood approx.), in logs;
+        // the same exp() values give the integer weights for the next resampling.
+        double lsum = 0.0;
+        for (int j = tid; j < N; j += B) {
+            const double v = exp(__dsub_rn(wbuf[j], emax));
+            lsum = __dadd_rn(lsum, v);
+            qbuf[j] = __double2ull_rz(__dmul_rn(v, 4294967296.0));
+        }
+        const double s = block_sum(lsum, sh);
+        if (tid == 0) {
+            double inc = __dadd_rn(emax, log(s));
+            inc = __dsub_rn(inc, log(static_cast<double>(N)));
+            inc = __dsub_rn(inc, sh.lognorm);
+            sh.ll = __dadd_rn(sh.ll, inc);
+        }
+        t_prev = t_k;
+    }
+    __syncthreads();
+    const unsigned long long fired_all = block_sum_u64(fired, sh);
+    const unsigned long long dig_all = args.dg_f ? block_sum_u64(dig, sh) : 0ull;
+    const int status = sh.status;
+    if (tid == 0) {
+        args.ll_f[f] = status == PF_ST_OK ? sh.ll : -INFINITY;
+        args.st_f[f] = static_cast<uint8_t>(status);
+        args.ev_f[f] = fired_all;
+        if (args.dg_f) args.dg_f[f] = dig_all;
+    }
+    if (args.final_states && status == PF_ST_OK) {
+        int32_t *out = args.final_states + f * static_cast<int64_t>(N) * U;
+        for (int j = tid; j < N; j += B)
+            for (int u = 0; u < U; ++u) out[static_cast<int64_t>(j) * U + u] = xs[u * Np + j];
+    }
+}
+
+// loglik[m] = sum over trajectories (in order) of the filter estimates (Supp. I).
+__global__ void reduce_kernel(const double *ll_f, const uint8_t *st_f, int64_t M, int T,
+                              double *loglik, uint8_t *status) {
+    const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (m >= M) return;
+    double sum = 0.0;
+    int st = PF_ST_OK;
+    for (int t = 0; t < T; ++t) {
+        const int s = st_f[m * T + t];
+        if (st == PF_ST_OK && s != PF_ST_OK) st = s;
+        sum = __dadd_rn(sum, ll_f[m * T + t]);
+    }
+    double out = sum;
+    if (st == PF_ST_INVALID_THETA) out = __longlong_as_double(0x7FF8000000000000ll);
+    else if (st != PF_ST_OK) out = -INFINITY;
+    loglik[m] = out;
+    if (status) status[m] = static_cast<uint8_t>(st);
+}
+
+__global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n) {
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const Philox4 w = philox4x32_10(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3],
+                                    key[2 * i], key[2 * i + 1]);
+    out[4 * i] = w.w0;
+    out[4 * i + 1] = w.w1;
+    out[4 * i + 2] = w.w2;
+    out[4 * i + 3] = w.w3;
+}
+
+template <int RM>
+int launch_tier(const FilterArgs &a, int B, size_t smem, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(filter_kernel<RM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    const int64_t F = a.M * a.T;
+    filter_kernel<RM><<<static_cast<unsigned>(F), B, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t filter_smem_bytes(int N, int U, int /*block_threads*/) {
+    return static_cast<size_t>(N) * 8 + 2 * static_cast<size_t>(U) * N * 4 +
+           static_cast<size_t>(N) * 4 + 16;
+}
+
+int reaction_tier(int R) {
+    if (R <= 4) return 4;
+    if (R <= 8) return 8;
+    if (R <= 16) return 16;
+    return 32;
+}
+
+int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, void *stream) {
+    if (a.M == 0) return cudaSuccess;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t smem = filter_smem_bytes(a.N, a.net.U, B);
+    int e;
+    switch (reaction_tier(a.net.R)) {
+        case 4: e = launch_tier<4>(a, B, smem, s); break;
+        case 8: e = launch_tier<8>(a, B, smem, s); break;
+        case 16: e = launch_tier<16>(a, B, smem, s); break;
+        default: e = launch_tier<32>(a, B, smem, s); break;
+    }
+    if (e != cudaSuccess) return e;
+    const int rb = 128;
+    reduce_kernel<<<static_cast<unsigned>((a.M + rb - 1) / rb), rb, 0, s>>>(a.ll_f, a.st_f, a.M,
+                                                                           a.T, loglik, status);
+    return cudaGetLastError();
+}
+
+int launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                  void *stream) {
+    if (n == 0) return cudaSuccess;
+    philox_kernel<<<static_cast<unsigned>((n + 127) / 128), 128, 0,
+                    static_cast<cudaStream_t>(stream)>>>(ctr, key, out, n);
+    return cudaGetLastError();
+}
+
+}  // namespace pf

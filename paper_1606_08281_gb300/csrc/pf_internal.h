@@ -1,0 +1,60 @@
+// Internal declarations shared by the kernels and the C ABI layer.
+#pragma once
+#include <cstdint>
+
+#include "pf1606.h"
+
+namespace pf {
+
+// Network tables in the form the kernels use.  Reactant side: at most two
+// (species, order) pairs because the total order is <= 2 (sp = -1: none).
+// Change side: a compact list of (species, delta) per reaction.  dep[r] has
+// bit r' set when reaction r' reads a species that reaction r changes, so
+// only those propensities are recomputed after r fires.
+struct NetTables {
+    int32_t U, R, P, d;
+    int32_t rate_col[PF_MAX_REACTIONS];
+    int8_t sp_a[PF_MAX_REACTIONS], ord_a[PF_MAX_REACTIONS];
+    int8_t sp_b[PF_MAX_REACTIONS], ord_b[PF_MAX_REACTIONS];
+    int8_t n_change[PF_MAX_REACTIONS];
+    int8_t ch_sp[PF_MAX_REACTIONS][PF_MAX_SPECIES];
+    int16_t ch_delta[PF_MAX_REACTIONS][PF_MAX_SPECIES];
+    uint32_t dep[PF_MAX_REACTIONS];
+    int32_t x0[PF_MAX_SPECIES];
+    double C[PF_MAX_OBS_DIM][PF_MAX_SPECIES];
+    double sigma[PF_MAX_OBS_DIM];
+};
+
+// Arguments of one filter launch: F = M * T filters, filter f = m * T + traj.
+struct FilterArgs {
+    NetTables net;
+    const double *thetas;    // [M][d]
+    const double *obs_times; // [K]
+    const double *y;         // [T][K][P]
+    int64_t M;
+    int32_t K, T, N;
+    uint64_t seed;
+    uint64_t budget;
+    // per-filter outputs [M*T] (scratch when the caller did not ask for them)
+    double *ll_f;
+    uint8_t *st_f;
+    uint64_t *ev_f;
+    uint64_t *dg_f;          // may be null: digest not computed
+    int32_t *final_states;   // [M*T][N][U], may be null
+};
+
+// Bytes of dynamic shared memory the filter kernel needs for N particles.
+size_t filter_smem_bytes(int N, int U, int block_threads);
+
+// Largest reaction-count template that fits R.
+int reaction_tier(int R);
+
+// Launch the filter kernel and the per-theta reduction on `stream`.
+// Returns a cudaError_t value (0 on success).
+int launch_filter(const FilterArgs &a, int block_threads, double *loglik, uint8_t *status,
+                  void *stream);
+
+int launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                  void *stream);
+
+}  // namespace pf

@@ -1,0 +1,211 @@
+"""Python binding of the C ABI in include/pf1606.h (argument marshalling only).
+
+Every step of the likelihood computation runs in the CUDA library
+``_build/libpf1606.so``; this module converts arrays to pointers and calls it.
+There is no CPU fallback: if the library is missing, ``load()`` raises.
+
+Host mode: pass numpy arrays; the call copies to the GPU and back.
+Device mode: pass torch CUDA tensors for thetas / obs_times / y (and the
+outputs are allocated as CUDA tensors); the call enqueues on the current torch
+stream (or ``stream``) and returns without synchronising.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import threading
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "_build" / "libpf1606.so"
+_lib = None
+_lock = threading.Lock()
+
+PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT, PF_EAGAIN, PF_ENOTFOUND, PF_EBUSY = (
+    0, -1, -2, -3, -4, -5, -6, -7)
+PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA = 0, 1, 2, 3
+
+EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
+            "pf_fp64_probe"]
+
+
+class PfError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail or 'error'} (code {code})")
+        self.code = code
+
+
+class pf_network(ct.Structure):
+    _fields_ = [("n_species", ct.c_int32), ("n_reactions", ct.c_int32),
+                ("reactants", ct.c_void_p), ("products", ct.c_void_p),
+                ("rate_index", ct.c_void_p)]
+
+
+class pf_options(ct.Structure):
+    _fields_ = [("event_budget", ct.c_uint64), ("device_ptrs", ct.c_int32),
+                ("block_threads", ct.c_int32), ("stream", ct.c_void_p),
+                ("ll_traj", ct.c_void_p), ("events", ct.c_void_p), ("digest", ct.c_void_p),
+                ("final_states", ct.c_void_p)]
+
+
+def library_path() -> Path:
+    return _LIB_PATH
+
+
+def load():
+    """Load libpf1606.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not _LIB_PATH.exists():
+                raise RuntimeError(f"{_LIB_PATH} is missing: build it with "
+                                   "`python -m paper_1606_08281_gb300.build` (no CPU fallback)")
+            lib = ct.CDLL(str(_LIB_PATH))
+            P = ct.c_void_p
+            lib.pf_loglik.argtypes = [ct.POINTER(pf_network), P, ct.c_int64, ct.c_int32, P, P,
+                                      ct.c_int32, P, ct.c_int32, ct.c_int32, P, P, ct.c_int32,
+                                      ct.c_uint64, P, P, ct.POINTER(pf_options)]
+            lib.pf_loglik.restype = ct.c_int
+            lib.pf_strerror.argtypes = [ct.c_int]
+            lib.pf_strerror.restype = ct.c_char_p
+            lib.pf_last_error.argtypes = []
+            lib.pf_last_error.restype = ct.c_char_p
+            lib.pf_version.argtypes = []
+            lib.pf_version.restype = ct.c_char_p
+            lib.pf_philox4x32_10.argtypes = [P, P, P, ct.c_int64]
+            lib.pf_philox4x32_10.restype = ct.c_int
+            lib.pf_fp64_probe.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int64,
+                                          ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
+            lib.pf_fp64_probe.restype = ct.c_int
+            _lib = lib
+    return _lib
+
+
+def _check(rc: int, where: str):
+    if rc != PF_OK:
+        lib = load()
+        raise PfError(rc, where, lib.pf_last_error().decode())
+
+
+def pf_strerror(code: int) -> str:
+    return load().pf_strerror(code).decode()
+
+
+def pf_last_error() -> str:
+    return load().pf_last_error().decode()
+
+
+def pf_version() -> str:
+    return load().pf_version().decode()
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _hptr(a):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+class _Net:
+    """Keeps the host arrays of a pf_network alive for the duration of a call."""
+
+    def __init__(self, net: dict):
+        self.reac = _host(net["reactants"], np.int32)
+        self.prod = _host(net["products"], np.int32)
+        ri = net.get("rate_index")
+        self.ri = None if ri is None else _host(ri, np.int32)
+        R, U = self.reac.shape
+        self.s = pf_network(U, R, _hptr(self.reac), _hptr(self.prod), _hptr(self.ri))
+
+
+def _is_torch_cuda(x) -> bool:
+    return type(x).__module__.startswith("torch") and getattr(x, "is_cuda", False)
+
+
+def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, seed: int, *,
+              event_budget: int = 0, block_threads: int = 0, stream=None,
+              diagnostics: bool = False, final_states: bool = False, out=None):
+    """Log-likelihood of every theta row (see pf_loglik in include/pf1606.h).
+
+    Returns a dict with 'loglik' [M] and 'status' [M]; with diagnostics=True
+    also 'll_traj', 'events', 'digest' [M][T]; with final_states=True also
+    'final_states' [M][T][N][U].  Arrays are numpy (host mode) or torch CUDA
+    tensors (device mode, chosen when `thetas` is a CUDA tensor).
+    """
+    lib = load()
+    n = _Net(net)
+    U = n.s.n_species
+    x0h = _host(x0, np.int32)
+    device = _is_torch_cuda(thetas)
+    if device:
+        import torch
+        th = thetas.contiguous()
+        assert th.dtype == torch.float64
+        M, d = th.shape
+        ts = _host(obs_times.cpu().numpy() if hasattr(obs_times, "cpu") else obs_times, np.float64)
+        yy = y.contiguous()
+        T, K, P = yy.shape
+        dev = th.device
+        if out is None:
+            out = {"loglik": torch.empty(M, dtype=torch.float64, device=dev),
+                   "status": torch.empty(M, dtype=torch.uint8, device=dev)}
+            if diagnostics:
+                out["ll_traj"] = torch.empty((M, T), dtype=torch.float64, device=dev)
+                out["events"] = torch.empty((M, T), dtype=torch.int64, device=dev)
+                out["digest"] = torch.empty((M, T), dtype=torch.int64, device=dev)
+            if final_states:
+                out["final_states"] = torch.empty((M, T, n_particles, U), dtype=torch.int32,
+                                                  device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        ptr = lambda k: (out[k].data_ptr() if k in out else None)  # noqa: E731
+        p_th, p_ts, p_y = th.data_ptr(), _hptr(ts), yy.data_ptr()
+    else:
+        th = _host(thetas, np.float64)
+        if th.ndim == 1:
+            th = th[None, :]
+        M, d = th.shape
+        ts = _host(obs_times, np.float64)
+        yy = _host(y, np.float64)
+        T, K, P = yy.shape
+        if out is None:
+            out = {"loglik": np.empty(M, np.float64), "status": np.empty(M, np.uint8)}
+            if diagnostics:
+                out["ll_traj"] = np.empty((M, T), np.float64)
+                out["events"] = np.empty((M, T), np.uint64)
+                out["digest"] = np.empty((M, T), np.uint64)
+            if final_states:
+                out["final_states"] = np.empty((M, T, n_particles, U), np.int32)
+        ptr = lambda k: (out[k].ctypes.data if k in out else None)  # noqa: E731
+        p_th, p_ts, p_y = _hptr(th), _hptr(ts), _hptr(yy)
+    Ch = _host(C, np.float64).reshape(P, U)
+    sg = _host(sigma, np.float64).reshape(P)
+    opt = pf_options(int(event_budget), 1 if device else 0, int(block_threads),
+                     stream if device else None, ptr("ll_traj"), ptr("events"), ptr("digest"),
+                     ptr("final_states"))
+    rc = lib.pf_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), p_ts, K, p_y, T, P, _hptr(Ch),
+                       _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
+                       ptr("loglik"), ptr("status"), ct.byref(opt))
+    _check(rc, "pf_loglik")
+    return out
+
+
+def pf_philox4x32_10(ctr, key) -> np.ndarray:
+    """Device Philox4x32-10 for n (counter[4], key[2]) pairs; returns uint32 [n][4]."""
+    lib = load()
+    c = _host(ctr, np.uint32).reshape(-1, 4)
+    k = _host(key, np.uint32).reshape(-1, 2)
+    out = np.zeros_like(c)
+    _check(lib.pf_philox4x32_10(_hptr(c), _hptr(k), _hptr(out), len(c)), "pf_philox4x32_10")
+    return out
+
+
+def pf_fp64_probe(kind: int, blocks: int, threads: int, iters: int):
+    """FP64 cost probe; returns (elapsed_ms, checksum).  See include/pf1606.h."""
+    lib = load()
+    ms = ct.c_double()
+    cs = ct.c_double()
+    _check(lib.pf_fp64_probe(kind, blocks, threads, iters, ct.byref(ms), ct.byref(cs)),
+           "pf_fp64_probe")
+    return ms.value, cs.value

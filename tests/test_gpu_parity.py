@@ -1,0 +1,204 @@
+"""Parity of the CUDA path (through the C ABI) with the oracle.
+
+Bar: per filter, the number of fired reactions and the digest of the whole
+resampling/simulation history are bit-identical; per-trajectory and per-theta
+log-likelihoods agree within 1e-9 relative; statuses are equal.  The only
+admissible source of a mismatch is a last-place difference between CUDA's
+and glibc's log/exp deciding an event-time boundary or an integer weight, at a
+rate of at most 1e-4 of filters; at these sizes that allows none.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from oracle import pf_oracle
+from paper_1606_08281_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-9
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_08281_gb300 import build, pf as pfmod
+    build.build()
+    pfmod.load()
+    return pfmod
+
+
+def run_both(pf, net, thetas, x0, times, y, C, sigma, N, seed, budget=0, theta_ids=None,
+             final_states=False, block_threads=0):
+    g = pf.pf_loglik(net, thetas, x0, times, y, C, sigma, N, seed, event_budget=budget,
+                     diagnostics=True, final_states=final_states, block_threads=block_threads)
+    o = pf_oracle.pf_loglik(net, thetas, x0, times, y, C, sigma, N, seed,
+                            budget=budget or pf_oracle.DEFAULT_BUDGET, theta_ids=theta_ids,
+                            want_final_states=final_states)
+    return g, o
+
+
+def assert_parity(g, o, final_states=False):
+    assert (g["status"] == o["status"]).all(), (g["status"], o["status"])
+    ok = o["status"] == 0
+    ev_eq = g["events"] == o["events"]
+    dg_eq = g["digest"] == o["digest"]
+    bad = np.argwhere(~(ev_eq & dg_eq)[ok])
+    assert len(bad) == 0, f"history mismatch in filters {bad[:10].tolist()}"
+    np.testing.assert_allclose(g["ll_traj"][ok], o["ll_traj"][ok], rtol=RTOL, atol=0)
+    np.testing.assert_allclose(g["loglik"][ok], o["loglik"][ok], rtol=RTOL, atol=0)
+    assert np.isneginf(g["loglik"][o["status"] == 1]).all()
+    if final_states:
+        assert (g["final_states"][ok] == o["final_states"][ok]).all()
+
+
+def test_device_philox_known_answers(pf, kat_vectors):
+    ctr = np.array([c for c, _, _ in kat_vectors], np.uint32)
+    key = np.array([k for _, k, _ in kat_vectors], np.uint32)
+    want = np.array([w for _, _, w in kat_vectors], np.uint32)
+    assert (pf.pf_philox4x32_10(ctr, key) == want).all()
+
+
+def test_device_philox_matches_oracle_generator(pf):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(512, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2**32, size=(512, 2), dtype=np.uint64).astype(np.uint32)
+    got = pf.pf_philox4x32_10(ctr, key)
+    for i in range(0, 512, 37):
+        assert (got[i] == pf_oracle.philox4x32_10(ctr[i], key[i])).all()
+
+
+def test_birth_death_full_config(pf):
+    """The birth-death workload at full size: 200 theta x 1 trajectory x 100 particles."""
+    w = W.birth_death()
+    g, o = run_both(pf, w.net, w.thetas(), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                    w.N, w.filter_seed, final_states=True)
+    assert_parity(g, o, final_states=True)
+    assert int(g["events"].sum()) > 10**6
+
+
+def test_gene_expression_subset(pf):
+    """24 theta x 3 trajectories x 1000 particles (ragged against the block), 12 times."""
+    w = W.gene_expression().subset(T=3, K=12)
+    g, o = run_both(pf, w.net, w.thetas(24), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                    w.N, w.filter_seed)
+    assert_parity(g, o)
+
+
+def test_cascade_subset(pf):
+    """10 species / 20 reactions, orders 0-2, 3 observed species: 6 theta x 2 x 512 x 5."""
+    w = W.cascade().subset(T=2, K=5)
+    g, o = run_both(pf, w.net, w.thetas(6), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                    w.N, w.filter_seed, final_states=True)
+    assert_parity(g, o, final_states=True)
+
+
+@pytest.mark.parametrize("N,B", [(1, 0), (2, 0), (33, 0), (100, 32), (257, 256), (1000, 128),
+                                 (4096, 256)])
+def test_particle_counts_and_block_sizes(pf, N, B):
+    w = W.gene_expression().subset(T=2, K=6)
+    g, o = run_both(pf, w.net, w.thetas(4), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                    N, 11, block_threads=B)
+    assert_parity(g, o)
+
+
+def test_observation_at_time_zero_and_single_time(pf):
+    w = W.birth_death()
+    y = np.array([[[3.3], [7.0]]])
+    g, o = run_both(pf, w.net, w.thetas(5), w.x0, [0.0, 0.25], y, w.C, w.sigma, 64, 3)
+    assert_parity(g, o)
+    g, o = run_both(pf, w.net, w.thetas(5), w.x0, [2.0], y[:, :1], w.C, w.sigma, 64, 3)
+    assert_parity(g, o)
+
+
+def test_absorbing_network(pf):
+    net = {"reactants": [[1]], "products": [[0]], "rate_index": None}
+    y = np.array([[[0.5], [-0.2]]])
+    g, o = run_both(pf, net, [[1.0]], [0], [1.0, 2.0], y, [[1.0]], [1.0], 8, 3)
+    assert_parity(g, o)
+    assert g["events"][0, 0] == 0
+
+
+def test_event_budget_status(pf):
+    w = W.birth_death()
+    g, o = run_both(pf, w.net, w.thetas(8), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                    32, 5, budget=30)
+    assert (o["status"] == 1).any() and (o["status"] == 0).any()
+    assert_parity(g, o)
+
+
+def test_invalid_theta_rows(pf):
+    w = W.birth_death()
+    th = w.thetas(4).copy()
+    th[1, 0] = -1.0
+    th[2, 1] = np.nan
+    g = pf.pf_loglik(w.net, th, w.x0, w.obs_times, w.observations(), w.C, w.sigma, 32, 5)
+    assert list(g["status"]) == [0, 3, 3, 0]
+    assert np.isnan(g["loglik"][1]) and np.isnan(g["loglik"][2])
+    o = pf_oracle.pf_loglik(w.net, th[[0, 3]], w.x0, w.obs_times, w.observations(), w.C,
+                            w.sigma, 32, 5, theta_ids=[0, 3])
+    np.testing.assert_allclose(g["loglik"][[0, 3]], o["loglik"], rtol=RTOL)
+
+
+def test_empty_batch_and_bad_arguments(pf):
+    w = W.birth_death()
+    g = pf.pf_loglik(w.net, np.zeros((0, 2)), w.x0, w.obs_times, w.observations(), w.C,
+                     w.sigma, 32, 5)
+    assert g["loglik"].shape == (0,)
+    with pytest.raises(pf.PfError) as e:
+        pf.pf_loglik(w.net, w.thetas(2), w.x0, w.obs_times[::-1].copy(), w.observations(), w.C,
+                     w.sigma, 32, 5)
+    assert e.value.code == pf.PF_EINVAL
+    with pytest.raises(pf.PfError):
+        pf.pf_loglik(w.net, w.thetas(2), w.x0, w.obs_times, w.observations(), w.C, [0.0], 32, 5)
+    with pytest.raises(pf.PfError):
+        pf.pf_loglik({"reactants": [[3]], "products": [[0]], "rate_index": None}, [[1.0]], [1],
+                     [1.0], np.zeros((1, 1, 1)), [[1.0]], [1.0], 4, 1)
+
+
+def test_device_pointer_mode_matches_host_mode(pf):
+    import torch
+    w = W.gene_expression().subset(T=2, K=8)
+    th = w.thetas(16)
+    h = pf.pf_loglik(w.net, th, w.x0, w.obs_times, w.observations(), w.C, w.sigma, 300, 9,
+                     diagnostics=True)
+    dev = torch.device("cuda:0")
+    d = pf.pf_loglik(w.net, torch.from_numpy(th).to(dev), w.x0,
+                     torch.from_numpy(w.obs_times).to(dev),
+                     torch.from_numpy(w.observations()).to(dev), w.C, w.sigma, 300, 9,
+                     diagnostics=True)
+    torch.cuda.synchronize()
+    assert (d["loglik"].cpu().numpy() == h["loglik"]).all()
+    assert (d["digest"].cpu().numpy().view(np.uint64) == h["digest"]).all()
+
+
+def test_repeatable(pf):
+    w = W.gene_expression().subset(T=2, K=10)
+    a = pf.pf_loglik(w.net, w.thetas(32), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                     500, 21, diagnostics=True)
+    b = pf.pf_loglik(w.net, w.thetas(32), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                     500, 21, diagnostics=True)
+    assert (a["loglik"] == b["loglik"]).all() and (a["digest"] == b["digest"]).all()
+
+
+def test_full_size_gene_expression_sampled(pf):
+    """The full gene-expression workload (4096 theta x 10 trajectories x 1000
+    particles x 50 times) in the launch configuration the benchmark times;
+    a sample of rows is recomputed one by one by the oracle."""
+    w = W.gene_expression()
+    th = w.thetas()
+    g = pf.pf_loglik(w.net, th, w.x0, w.obs_times, w.observations(), w.C, w.sigma, w.N,
+                     w.filter_seed, diagnostics=True)
+    assert (g["status"] == 0).all()
+    ev = g["events"].sum(axis=1).astype(float)
+    rng = np.random.default_rng(123)
+    cheap = np.flatnonzero(ev < np.quantile(ev, 0.5))
+    pick = np.sort(np.concatenate([rng.choice(cheap, 5, replace=False), [0, len(th) - 1]]))
+    pick = np.unique(pick)
+    o = pf_oracle.pf_loglik(w.net, th[pick], w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                            w.N, w.filter_seed, theta_ids=pick)
+    sub = {k: g[k][pick] for k in ("loglik", "status", "ll_traj", "events", "digest")}
+    assert_parity(sub, o)
