@@ -209,6 +209,11 @@ def main() -> None:
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--max-theta", type=int, default=0,
+                    help="profiling case: only the first M' theta rows (not a bench line)")
+    ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--probe-only", action="store_true",
+                    help="run the FP64 cost probe alone and print it")
     a = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -229,10 +234,16 @@ def main() -> None:
     if world > 1:
         dist.barrier()
     pf.load()
+    if a.probe_only:
+        print(json.dumps(fp64_probe(pf)), flush=True)
+        return
 
     w = W.get(a.workload)
+    if a.max_theta:
+        w.M = min(w.M, a.max_theta)
     th_np = w.thetas() if rank == 0 else W.log_uniform(
         np.random.default_rng(w.theta_seed + 7919 * rank), w.prior_lo, w.prior_hi, w.M)
+    th_np = np.ascontiguousarray(th_np[: w.M])
     y_np = w.observations()
     th = torch.from_numpy(th_np).to(dev)
     yd = torch.from_numpy(y_np).to(dev)
@@ -254,7 +265,7 @@ def main() -> None:
     assert int((out["status"] != 0).sum().item()) == 0
 
     # FP64 cost probe: FMA peak and the price of log / division
-    probe = fp64_probe(pf)
+    probe = None if a.no_probe else fp64_probe(pf)
 
     clocks = ClockSampler(local)
     if world > 1:
@@ -297,7 +308,7 @@ def main() -> None:
                      w.filter_seed, out=host_out)
         e2e_times.append(time.perf_counter() - t0)
     assert np.array_equal(host_out["loglik"], out["loglik"].cpu().numpy()) or rank != 0
-    e2e_s = float(np.mean(e2e_times))
+    e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
     if world > 1:
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -308,8 +319,10 @@ def main() -> None:
         cpu = oracle_baseline(a.workload, a.cpu_seconds)
 
     if rank == 0:
-        f_log = FP64_FLOPS_LOG if FP64_FLOPS_LOG is not None else probe["log_fma_equiv_flops"]
-        f_div = FP64_FLOPS_DIV if FP64_FLOPS_DIV is not None else probe["div_fma_equiv_flops"]
+        f_log = FP64_FLOPS_LOG if FP64_FLOPS_LOG is not None else (
+            probe["log_fma_equiv_flops"] if probe else float("nan"))
+        f_div = FP64_FLOPS_DIV if FP64_FLOPS_DIV is not None else (
+            probe["div_fma_equiv_flops"] if probe else float("nan"))
         fpe = flops_per_event(w.R, f_log, f_div)
         achieved = fpe * ev_step / (local_ms * 1e-3) / 1e12
         value = world * M / (ms * 1e-3)
