@@ -42,17 +42,24 @@ FP64_FLOPS_PER_SM_CLK = 4.0
 N_SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = FP64_FLOPS_PER_SM_CLK * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
-# FP64 flops priced per call of log() and IEEE division (FMA = 2 flops), from
-# ncu FP64 instruction counters on the pf_fp64_probe kernels; None = price
-# them live from the probe's timing relative to the FMA peak.
-FP64_FLOPS_LOG = None
-FP64_FLOPS_DIV = None
+# FP64 flops (FMA = 2) of the two transcendental steps of an SSA event, as the
+# library computes them, counted by ncu's FP64 instruction counters on the
+# pf_fp64_probe kernels: the table-driven -log(u) is 1 DADD + 2 DMUL +
+# 6 DFMA + 2 DADD (= 17 flops, 11 operations); the IEEE division is
+# 7 DFMA + 1 DMUL (= 15 flops, 8 operations).
+FP64_FLOPS_LOG, FP64_OPS_LOG = 17.0, 11.0
+FP64_FLOPS_DIV, FP64_OPS_DIV = 15.0, 8.0
 
 
-def flops_per_event(R: int, f_log: float, f_div: float) -> float:
+def flops_per_event(R: int) -> float:
     """Algorithmic FP64 flops of one direct-method SSA event: R propensity
-    products and R prefix additions, u2*a0, t + tau, one log, one division."""
-    return 2.0 * R + 2.0 + f_log + f_div
+    products, R-1 prefix additions, u2*a0, t + tau, one log, one division."""
+    return R + (R - 1) + 1.0 + 1.0 + FP64_FLOPS_LOG + FP64_FLOPS_DIV
+
+
+def ops_per_event(R: int) -> float:
+    """The same work in FP64 pipe operations (each DFMA/DMUL/DADD = 1)."""
+    return R + (R - 1) + 1.0 + 1.0 + FP64_OPS_LOG + FP64_OPS_DIV
 
 
 # ---------------------------------------------------------------- clocks
@@ -320,12 +327,10 @@ def main() -> None:
         cpu = oracle_baseline(a.workload, a.cpu_seconds)
 
     if rank == 0:
-        f_log = FP64_FLOPS_LOG if FP64_FLOPS_LOG is not None else (
-            probe["log_fma_equiv_flops"] if probe else float("nan"))
-        f_div = FP64_FLOPS_DIV if FP64_FLOPS_DIV is not None else (
-            probe["div_fma_equiv_flops"] if probe else float("nan"))
-        fpe = flops_per_event(w.R, f_log, f_div)
+        fpe = flops_per_event(w.R)
         achieved = fpe * ev_step / (local_ms * 1e-3) / 1e12
+        ops_rate = ops_per_event(w.R) * ev_step / (local_ms * 1e-3) / 1e12
+        ops_peak = FP64_PEAK_TFLOPS / 2.0
         value = world * M / (ms * 1e-3)
         h2d = th_np.nbytes + y_np.nbytes + w.obs_times.nbytes
         d2h = M * 8 + M
@@ -345,6 +350,8 @@ def main() -> None:
                          "traffic": None,
                          "kernel": "filter_kernel (FP64 pipe)",
                          "flops_per_event": fpe,
+                         "fp64_ops_per_event": ops_per_event(w.R),
+                         "fp64_pipe_ops_frac": ops_rate / ops_peak,
                          "peak_source": "nominal GB300 FP64 1.25 TFLOP/s = 4 flops/SM/clk x "
                                         "152 SMs x 2070 MHz",
                          "kernel_ms": local_ms},
@@ -361,7 +368,8 @@ def fp64_probe(pf) -> dict:
     blocks, threads = 152 * 4, 256
     res = {}
     iters = {0: 4096, 1: 256, 2: 512}
-    for kind in (0, 1, 2):
+    iters[3] = 512
+    for kind in (0, 1, 2, 3):
         pf.pf_fp64_probe(kind, blocks, threads, 16)          # warm-up
         ms, _ = pf.pf_fp64_probe(kind, blocks, threads, iters[kind])
         res[kind] = ms
@@ -369,7 +377,9 @@ def fp64_probe(pf) -> dict:
     fma_rate = ops * iters[0] / (res[0] * 1e-3)            # FMA instructions per second
     log_rate = ops * iters[1] / (res[1] * 1e-3)            # log calls (+2 adds) per second
     div_rate = ops * iters[2] / (res[2] * 1e-3)
+    mylog_rate = ops * iters[3] / (res[3] * 1e-3)
     return {
+        "table_log_per_s": mylog_rate,
         "fma_tflops": 2 * fma_rate / 1e12,
         "log_per_s": log_rate, "div_per_s": div_rate,
         # cost of one call in FMA-equivalent flops (2 per FMA), minus its two adds

@@ -169,7 +169,9 @@ int pf_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, in
  *   kind 0: fused multiply-add (the FP64 pipe's peak rate: 16 flops per
  *           iteration and thread);
  *   kind 1: log() plus two additions per chain step;
- *   kind 2: IEEE division plus two additions per chain step.
+ *   kind 2: IEEE division plus two additions per chain step;
+ *   kind 3: the library's table-driven -log(u) (pf_neg_log_u53) plus one
+ *           addition per chain step.
  * With ncu's FP64 instruction counters this prices one log() and one division
  * in FP64 operations, the per-event cost model of the SSA kernel's roofline.
  * Returns PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.  Allocates and frees its
@@ -177,6 +179,16 @@ int pf_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, in
  */
 int pf_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters,
                   double *elapsed_ms, double *checksum);
+
+/*
+ * pf_neg_log_u53 -- the device logarithm the SSA kernel uses for the waiting
+ * time tau = -log(u1) / a0 (Sec. "The stochastic birth-death Model": SSA),
+ * exposed for accuracy tests: out[i] = -log(v[i] * 2^-53) for
+ * 1 <= v[i] <= 2^53 (u1 in (0, 1]).  Table-driven (Tang, ACM TOMS 16(4),
+ * 1990), 11 FP64 operations.  Host pointers; synchronous.  Returns PF_OK,
+ * PF_EINVAL (a v[i] out of range), PF_ENOMEM or PF_ECUDA.
+ */
+int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n);
 
 #ifdef __cplusplus
 }

@@ -5,6 +5,12 @@
 // Approximation using particle filter"):
 //   resample by the previous weights -> simulate every particle to t_k with
 //   the direct-method SSA -> Gaussian weight -> log-sum-exp increment.
+// Within one interval the particles form a pool: each lane simulates one
+// particle and, when that particle reaches t_k, takes the next unclaimed one
+// (a shared-memory counter), so warps stay full although particles fire very
+// different numbers of reactions.  GB300's FP64 pipe spends the same 16
+// cycles on a warp instruction whatever its active-lane count, so idle lanes
+// would cost FP64 throughput directly.
 // The whole particle population lives in shared memory: states int32 [U][N]
 // (two buffers for the gather), the weights / integer-weight prefix sums
 // (8 bytes per particle, reused), and the ancestor indices.  Nothing of the
@@ -20,6 +26,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "fastmath.cuh"
 #include "pf_internal.h"
 #include "philox.cuh"
 
@@ -41,6 +48,8 @@ struct SharedHead {
     double lognorm;
     int status;
     int valid;
+    int pool_next;
+    LogTab logt;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -60,67 +69,91 @@ __device__ __forceinline__ double propensity(int r, const SharedHead &sh, const 
     if (sa >= 0) h = binom_small(xs[sa * Np + j], n.ord_a[r]);
     const int sb = n.sp_b[r];
     if (sb >= 0) h *= binom_small(xs[sb * Np + j], n.ord_b[r]);
-    return __dmul_rn(sh.rate[r], __ll2double_rn(h));
+    return __dmul_rn(sh.rate[r], count_to_double(h));
 }
 
-template <int RM>
-__device__ __forceinline__ double prefix_sums(const double (&a)[RM], double (&S)[RM], int R) {
-    double run = a[0];
-    S[0] = run;
-#pragma unroll
-    for (int r = 1; r < RM; ++r) {
-        if (r < R) run = __dadd_rn(run, a[r]);
-        S[r] = run;
-    }
-    return run;
-}
+// Bits of a non-negative double: for x, y >= +0, x <= y iff bits(x) <= bits(y)
+// as signed integers, so these compares run on the integer pipes.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 
-// Advance particle slot j from t to t_end by Gillespie's direct method.
-// Returns PF_ST_OK or PF_ST_BUDGET; `fired` counts reactions that fired.
+// Simulate every particle of the filter from t_prev to t_end by Gillespie's
+// direct method (Supp. I, "Simulate X_t"; Sec. "The stochastic birth-death
+// Model": SSA).  Lanes draw particles from a pool; each lane runs one direct-
+// method step per loop trip.  Returns through sh.status (PF_ST_BUDGET when a
+// particle needed more than `budget` draws); `fired` counts reactions.
 template <int RM>
-__device__ int ssa_advance(const SharedHead &sh, int *xs, int Np, int j, double t, double t_end,
-                           uint32_t key0, uint32_t key1, uint32_t lane, uint32_t mrow,
-                           uint64_t budget, unsigned long long &fired) {
+__device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N, double t_prev, double t_end,
+                             uint32_t key0, uint32_t key1, uint32_t lane, uint32_t mrow,
+                             uint64_t budget, unsigned long long &fired) {
     const int R = sh.net.R;
+    const uint32_t all = (R >= 32) ? 0xFFFFFFFFu : ((1u << R) - 1u);
+    const long long t_end_bits = dbits(t_end);
     double a[RM], S[RM];
 #pragma unroll
-    for (int r = 0; r < RM; ++r) a[r] = (r < R) ? propensity(r, sh, xs, Np, j) : 0.0;
-    double a0 = prefix_sums<RM>(a, S, R);
-    uint64_t draws = 0;
-    for (;;) {
-        if (!(a0 > 0.0)) return PF_ST_OK;  // absorbing state
-        if (draws >= budget) return PF_ST_BUDGET;
-        const Philox4 w = philox4x32_10(static_cast<uint32_t>(draws), static_cast<uint32_t>(j),
-                                        lane, mrow, key0, key1);
-        ++draws;
-        const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
-        const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
-        const double u1 = scaled_u53((r0 >> 11) + 1ull);        // (0, 1]
-        const uint64_t v2 = r1 >> 11;
-        const double u2 = v2 ? scaled_u53(v2) : 0.0;            // [0, 1)
-        const double tau = __ddiv_rn(-log(u1), a0);
-        const double t_next = __dadd_rn(t, tau);
-        if (t_next > t_end) return PF_ST_OK;  // pending event lies past t_end: discard
-        const double target = __dmul_rn(u2, a0);
-        int chosen = 0;
-#pragma unroll
-        for (int r = 0; r < RM; ++r) chosen += (r < R && S[r] <= target) ? 1 : 0;
-        if (chosen >= R) {  // rounding guard: last reaction that can fire
-            chosen = 0;
-#pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if (r < R && a[r] > 0.0) chosen = r;
-        }
-        const int nch = sh.net.n_change[chosen];
-        for (int i = 0; i < nch; ++i)
-            xs[sh.net.ch_sp[chosen][i] * Np + j] += sh.net.ch_delta[chosen][i];
-        t = t_next;
-        ++fired;
-        const uint32_t deps = sh.net.dep[chosen];
+    for (int r = 0; r < RM; ++r) a[r] = 0.0;
+    int j = atomicAdd(&sh.pool_next, 1);
+    bool active = j < N;
+    double t = t_prev;
+    uint32_t draws = 0;
+    uint32_t mask = all;  // propensities to (re)compute before the next step
+    while (__any_sync(kFull, active)) {
+        if (!active) continue;
 #pragma unroll
         for (int r = 0; r < RM; ++r)
-            if ((deps >> r) & 1u) a[r] = propensity(r, sh, xs, Np, j);
-        a0 = prefix_sums<RM>(a, S, R);
+            if ((mask >> r) & 1u) a[r] = propensity(r, sh, xs, Np, j);
+        double run = a[0];
+        S[0] = run;
+#pragma unroll
+        for (int r = 1; r < RM; ++r) {
+            if (r < R) run = __dadd_rn(run, a[r]);
+            S[r] = run;
+        }
+        const double a0 = run;
+        bool done;
+        if (dbits(a0) == 0) {
+            done = true;                                   // absorbing: nothing can fire
+        } else if (draws >= budget) {
+            sh.status = PF_ST_BUDGET;
+            done = true;
+        } else {
+            const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(j), lane, mrow, key0, key1);
+            ++draws;
+            const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+            const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
+            // tau = -log(u1) / a0 with u1 = ((r0 >> 11) + 1) 2^-53 in (0, 1]
+            const double tau = __ddiv_rn(neg_log_u53((r0 >> 11) + 1ull, sh.logt), a0);
+            const double t_next = __dadd_rn(t, tau);
+            if (dbits(t_next) > t_end_bits) {
+                done = true;                               // the event lies past t_end
+            } else {
+                const uint64_t v2 = r1 >> 11;              // u2 = v2 2^-53 in [0, 1)
+                const double target = __dmul_rn(v2 ? scaled_u53(v2) : 0.0, a0);
+                const long long tb = dbits(target);
+                int chosen = 0;                            // first r with target < S_r
+#pragma unroll
+                for (int r = 0; r < RM; ++r) chosen += (r < R && dbits(S[r]) <= tb) ? 1 : 0;
+                if (chosen >= R) {                         // rounding guard
+                    chosen = 0;
+#pragma unroll
+                    for (int r = 0; r < RM; ++r)
+                        if (r < R && dbits(a[r]) != 0) chosen = r;
+                }
+                const int nch = sh.net.n_change[chosen];
+                for (int i = 0; i < nch; ++i)
+                    xs[sh.net.ch_sp[chosen][i] * Np + j] += sh.net.ch_delta[chosen][i];
+                t = t_next;
+                ++fired;
+                mask = sh.net.dep[chosen];
+                done = false;
+            }
+        }
+        if (done) {
+            j = atomicAdd(&sh.pool_next, 1);
+            active = j < N;
+            t = t_prev;
+            draws = 0;
+            mask = all;
+        }
     }
 }
 
@@ -219,7 +252,7 @@ __device__ void block_scan_u64(unsigned long long *q, int N, SharedHead &sh) {
 
 // ------------------------------------------------------------------ kernels
 template <int RM>
-__global__ void __launch_bounds__(256, 1) filter_kernel(const FilterArgs args) {
+__global__ void __launch_bounds__(256, 2) filter_kernel(const FilterArgs args) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SharedHead sh;
     const int tid = threadIdx.x, B = blockDim.x;
@@ -249,6 +282,7 @@ __global__ void __launch_bounds__(256, 1) filter_kernel(const FilterArgs args) {
         sh.lognorm = __dadd_rn(ln, __dmul_rn(0.5 * static_cast<double>(P), log(2.0 * M_PI)));
     }
     if (tid < R) sh.rate[tid] = theta[args.net.rate_col[tid]];
+    load_log_table(sh.logt);
     __syncthreads();
     if (!sh.valid) {
         if (tid == 0) {
@@ -309,11 +343,9 @@ __global__ void __launch_bounds__(256, 1) filter_kernel(const FilterArgs args) {
 
         const double t_k = args.obs_times[k];
         if (t_k > t_prev) {
-            for (int j = tid; j < N; j += B) {
-                const int st = ssa_advance<RM>(sh, xs, Np, j, t_prev, t_k, key0, key1, lane, m32,
-                                               args.budget, fired);
-                if (st != PF_ST_OK) sh.status = st;
-            }
+            if (tid == 0) sh.pool_next = 0;
+            __syncthreads();
+            ssa_interval<RM>(sh, xs, Np, N, t_prev, t_k, key0, key1, lane, m32, args.budget, fired);
         }
         __syncthreads();
         if (sh.status != PF_ST_OK) break;

@@ -9,6 +9,7 @@
 
 #include <cstdint>
 
+#include "fastmath.cuh"
 #include "pf1606.h"
 
 namespace {
@@ -16,6 +17,9 @@ namespace {
 constexpr int kChains = 8;
 
 __global__ void probe_kernel(int kind, int64_t iters, double *out) {
+    __shared__ pf::LogTab tab;
+    pf::load_log_table(tab);
+    __syncthreads();
     double acc[kChains], x[kChains];
 #pragma unroll
     for (int c = 0; c < kChains; ++c) {
@@ -33,12 +37,23 @@ __global__ void probe_kernel(int kind, int64_t iters, double *out) {
                 acc[c] = __dadd_rn(acc[c], log(x[c]));
                 x[c] = __dadd_rn(x[c], 1e-12);
             }
-    } else {
+    } else if (kind == 2) {
         for (int64_t i = 0; i < iters; ++i)
 #pragma unroll
             for (int c = 0; c < kChains; ++c) {
                 acc[c] = __dadd_rn(acc[c], __ddiv_rn(1.5, x[c]));
                 x[c] = __dadd_rn(x[c], 1e-12);
+            }
+    } else {
+        uint64_t v[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c)
+            v[c] = (0x9E3779B97F4A7C15ull * (threadIdx.x + 977u * blockIdx.x + 131u * c)) >> 11;
+        for (int64_t i = 0; i < iters; ++i)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) {
+                acc[c] = __dadd_rn(acc[c], pf::neg_log_u53(v[c] + 1ull, tab));
+                v[c] = (v[c] * 6364136223846793005ull + 1442695040888963407ull) >> 11;
             }
     }
     double s = 0.0;
@@ -51,7 +66,7 @@ __global__ void probe_kernel(int kind, int64_t iters, double *out) {
 
 extern "C" int pf_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters,
                              double *elapsed_ms, double *checksum) {
-    if (kind < 0 || kind > 2 || blocks < 1 || threads < 32 || threads > 1024 || iters < 1 ||
+    if (kind < 0 || kind > 3 || blocks < 1 || threads < 32 || threads > 1024 || iters < 1 ||
         !elapsed_ms)
         return PF_EINVAL;
     double *d = nullptr;
@@ -76,4 +91,33 @@ extern "C" int pf_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int6
     cudaEventDestroy(e1);
     cudaFree(d);
     return err == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+namespace {
+__global__ void neg_log_kernel(const uint64_t *v, double *out, int64_t n) {
+    __shared__ pf::LogTab tab;
+    pf::load_log_table(tab);
+    __syncthreads();
+    const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = pf::neg_log_u53(v[i], tab);
+}
+}  // namespace
+
+extern "C" int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n) {
+    if (n < 0 || (n > 0 && (!v || !out))) return PF_EINVAL;
+    for (int64_t i = 0; i < n; ++i)
+        if (v[i] < 1 || v[i] > (1ull << 53)) return PF_EINVAL;
+    if (n == 0) return PF_OK;
+    uint64_t *dv = nullptr;
+    double *dout = nullptr;
+    if (cudaMalloc(&dv, n * sizeof(uint64_t)) != cudaSuccess) return PF_ENOMEM;
+    if (cudaMalloc(&dout, n * sizeof(double)) != cudaSuccess) { cudaFree(dv); return PF_ENOMEM; }
+    cudaError_t e = cudaMemcpy(dv, v, n * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        neg_log_kernel<<<static_cast<unsigned>((n + 255) / 256), 256>>>(dv, dout, n);
+        e = cudaMemcpy(out, dout, n * sizeof(double), cudaMemcpyDeviceToHost);
+    }
+    cudaFree(dv);
+    cudaFree(dout);
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
 }

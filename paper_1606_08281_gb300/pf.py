@@ -26,7 +26,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT, PF_EAGAIN, PF_ENOTFOUND, PF_
 PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA = 0, 1, 2, 3
 
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
-            "pf_fp64_probe"]
+            "pf_fp64_probe", "pf_neg_log_u53"]
 
 
 class PfError(RuntimeError):
@@ -77,6 +77,8 @@ def load():
             lib.pf_fp64_probe.argtypes = [ct.c_int32, ct.c_int32, ct.c_int32, ct.c_int64,
                                           ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)]
             lib.pf_fp64_probe.restype = ct.c_int
+            lib.pf_neg_log_u53.argtypes = [P, P, ct.c_int64]
+            lib.pf_neg_log_u53.restype = ct.c_int
             _lib = lib
     return _lib
 
@@ -209,3 +211,12 @@ def pf_fp64_probe(kind: int, blocks: int, threads: int, iters: int):
     _check(lib.pf_fp64_probe(kind, blocks, threads, iters, ct.byref(ms), ct.byref(cs)),
            "pf_fp64_probe")
     return ms.value, cs.value
+
+
+def pf_neg_log_u53(v) -> np.ndarray:
+    """The kernels' -log(v 2^-53), for 1 <= v <= 2^53 (device computation)."""
+    lib = load()
+    vv = _host(v, np.uint64).reshape(-1)
+    out = np.empty(len(vv), np.float64)
+    _check(lib.pf_neg_log_u53(_hptr(vv), _hptr(out), len(vv)), "pf_neg_log_u53")
+    return out

@@ -1,0 +1,60 @@
+"""Accuracy of the kernels' table-driven -log(u) against correctly rounded
+values computed with 40-digit decimal arithmetic."""
+from __future__ import annotations
+
+import math
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def exact_neg_log(v: int) -> float:
+    getcontext().prec = 40
+    return float(-(Decimal(v) / Decimal(2) ** 53).ln())
+
+
+def ulp_distance(a: float, b: float) -> int:
+    ia = np.array([a], np.float64).view(np.int64)[0]
+    ib = np.array([b], np.float64).view(np.int64)[0]
+    return abs(int(ia) - int(ib))
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_08281_gb300 import build, pf as pfmod
+    build.build()
+    return pfmod
+
+
+def test_neg_log_edge_values(pf):
+    vs = [1, 2, 3, 2**52 - 1, 2**52, 2**52 + 1, 2**53 - 1, 2**53, 3 * 2**50, 2**45 + 12345]
+    vs += [int(((256 + j) * 2**44 + d)) for j in (0, 1, 127, 128, 255) for d in (-1, 0, 1, 2**43)]
+    vs += [2**e for e in range(0, 54)]
+    vs = [v for v in vs if 1 <= v <= 2**53]
+    got = pf.pf_neg_log_u53(np.array(vs, np.uint64))
+    for v, g in zip(vs, got):
+        want = exact_neg_log(v)
+        assert ulp_distance(g, want) <= 1, (v, g, want)
+    assert got[vs.index(2**53)] == 0.0
+
+
+def test_neg_log_random_within_one_ulp(pf):
+    rng = np.random.default_rng(7)
+    v = (rng.integers(0, 2**63, size=20000, dtype=np.uint64) >> np.uint64(10)) + np.uint64(1)
+    v = np.minimum(v, np.uint64(2**53))
+    # also many values close to 1 (u1 near 1: the small-result regime)
+    near = np.uint64(2**53) - rng.integers(0, 2**30, size=5000, dtype=np.uint64)
+    v = np.concatenate([v, near])
+    got = pf.pf_neg_log_u53(v)
+    d = np.array([ulp_distance(g, exact_neg_log(int(x))) for g, x in zip(got, v)])
+    assert d.max() <= 1
+    assert np.mean(d == 0) > 0.99
+    # the same inputs through the host libm agree to within one ulp too
+    host = -np.log(v.astype(np.float64) * 2.0**-53)
+    assert np.max(np.abs(host - got) / np.maximum(np.spacing(np.abs(host)), 1e-300)) <= 2
