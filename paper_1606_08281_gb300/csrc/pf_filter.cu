@@ -49,6 +49,8 @@ struct SharedHead {
     int status;
     int valid;
     int pool_next;
+    int bucket[16];
+    float rate_f[PF_MAX_REACTIONS];  // FP32 copy of rate[], for cost estimates only
     LogTab logt;
 };
 
@@ -60,16 +62,41 @@ __device__ __forceinline__ long long binom_small(int x, int p) {
     return x >= 2 ? (xl * (xl - 1)) / 2 : 0;  // p == 2
 }
 
-// a_r = theta_rho(r) * prod_u binom(x_u, p_ru)  (Sec. "Chemical Reaction Networks")
-__device__ __forceinline__ double propensity(int r, const SharedHead &sh, const int *xs, int Np,
-                                             int j) {
-    const NetTables &n = sh.net;
+// Particle state of the lane's current particle: in registers when the
+// network has at most UM species (UM > 0), else read in place from shared
+// memory (UM == 0).
+template <int UM>
+struct Lane {
+    int x[UM > 0 ? UM : 1];
+    const int *xs;
+    int Np, j;
+    __device__ __forceinline__ int get(int sp) const {
+        if constexpr (UM > 0) {
+            int v = x[0];
+#pragma unroll
+            for (int u = 1; u < UM; ++u) v = (sp == u) ? x[u] : v;
+            return v;
+        } else {
+            return xs[sp * Np + j];
+        }
+    }
+};
+
+// h_r(x) = prod_u binom(x_u, p_ru)  (mass action, Sec. "Chemical Reaction Networks")
+template <int UM>
+__device__ __forceinline__ long long combos(int r, const NetTables &n, const Lane<UM> &L) {
     long long h = 1;
     const int sa = n.sp_a[r];
-    if (sa >= 0) h = binom_small(xs[sa * Np + j], n.ord_a[r]);
+    if (sa >= 0) h = binom_small(L.get(sa), n.ord_a[r]);
     const int sb = n.sp_b[r];
-    if (sb >= 0) h *= binom_small(xs[sb * Np + j], n.ord_b[r]);
-    return __dmul_rn(sh.rate[r], count_to_double(h));
+    if (sb >= 0) h *= binom_small(L.get(sb), n.ord_b[r]);
+    return h;
+}
+
+// a_r = theta_rho(r) * h_r(x)
+template <int UM>
+__device__ __forceinline__ double propensity(int r, const SharedHead &sh, const Lane<UM> &L) {
+    return __dmul_rn(sh.rate[r], count_to_double(combos<UM>(r, sh.net, L)));
 }
 
 // Bits of a non-negative double: for x, y >= +0, x <= y iff bits(x) <= bits(y)
@@ -78,21 +105,35 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 
 // Simulate every particle of the filter from t_prev to t_end by Gillespie's
 // direct method (Supp. I, "Simulate X_t"; Sec. "The stochastic birth-death
-// Model": SSA).  Lanes draw particles from a pool; each lane runs one direct-
-// method step per loop trip.  Returns through sh.status (PF_ST_BUDGET when a
-// particle needed more than `budget` draws); `fired` counts reactions.
-template <int RM>
-__device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N, double t_prev, double t_end,
-                             uint32_t key0, uint32_t key1, uint32_t lane, uint32_t mrow,
-                             uint64_t budget, unsigned long long &fired) {
-    const int R = sh.net.R;
+// Model": SSA).  Lanes take particles from a pool in the order `order`
+// (heaviest expected work first); each loop trip is one direct-method step of
+// every active lane.  Failure is reported through sh.status (PF_ST_BUDGET when
+// a particle needed more than `budget` draws); `fired` counts reactions.
+template <int RM, int UM>
+__device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, int N,
+                             double t_prev, double t_end, uint32_t key0, uint32_t key1,
+                             uint32_t lane, uint32_t mrow, uint64_t budget,
+                             unsigned long long &fired) {
+    const int R = sh.net.R, U = sh.net.U;
     const uint32_t all = (R >= 32) ? 0xFFFFFFFFu : ((1u << R) - 1u);
     const long long t_end_bits = dbits(t_end);
+    Lane<UM> L;
+    L.xs = xs;
+    L.Np = Np;
+    auto take = [&](bool &act) {
+        const int slot = atomicAdd(&sh.pool_next, 1);
+        act = slot < N;
+        L.j = act ? order[slot] : 0;
+        if constexpr (UM > 0) {
+#pragma unroll
+            for (int u = 0; u < UM; ++u) L.x[u] = (act && u < U) ? xs[u * Np + L.j] : 0;
+        }
+    };
     double a[RM], S[RM];
 #pragma unroll
     for (int r = 0; r < RM; ++r) a[r] = 0.0;
-    int j = atomicAdd(&sh.pool_next, 1);
-    bool active = j < N;
+    bool active;
+    take(active);
     double t = t_prev;
     uint32_t draws = 0;
     uint32_t mask = all;  // propensities to (re)compute before the next step
@@ -100,7 +141,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N, double t_pr
         if (!active) continue;
 #pragma unroll
         for (int r = 0; r < RM; ++r)
-            if ((mask >> r) & 1u) a[r] = propensity(r, sh, xs, Np, j);
+            if ((mask >> r) & 1u) a[r] = propensity<UM>(r, sh, L);
         double run = a[0];
         S[0] = run;
 #pragma unroll
@@ -116,7 +157,8 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N, double t_pr
             sh.status = PF_ST_BUDGET;
             done = true;
         } else {
-            const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(j), lane, mrow, key0, key1);
+            const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
+                                            key1);
             ++draws;
             const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
             const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
@@ -139,8 +181,15 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N, double t_pr
                         if (r < R && dbits(a[r]) != 0) chosen = r;
                 }
                 const int nch = sh.net.n_change[chosen];
-                for (int i = 0; i < nch; ++i)
-                    xs[sh.net.ch_sp[chosen][i] * Np + j] += sh.net.ch_delta[chosen][i];
+                for (int i = 0; i < nch; ++i) {
+                    const int sp = sh.net.ch_sp[chosen][i], dlt = sh.net.ch_delta[chosen][i];
+                    if constexpr (UM > 0) {
+#pragma unroll
+                        for (int u = 0; u < UM; ++u) L.x[u] += (sp == u) ? dlt : 0;
+                    } else {
+                        xs[sp * Np + L.j] += dlt;
+                    }
+                }
                 t = t_next;
                 ++fired;
                 mask = sh.net.dep[chosen];
@@ -148,13 +197,34 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N, double t_pr
             }
         }
         if (done) {
-            j = atomicAdd(&sh.pool_next, 1);
-            active = j < N;
+            if constexpr (UM > 0) {
+#pragma unroll
+                for (int u = 0; u < UM; ++u)
+                    if (u < U) xs[u * Np + L.j] = L.x[u];
+            }
+            take(active);
             t = t_prev;
             draws = 0;
             mask = all;
         }
     }
+}
+
+// Expected-work bucket of particle j for the interval (FP32, ordering only):
+// 15 - min(15, 1 + floor(log2(a0(x_j) * dt))), so heavy particles come first.
+__device__ __forceinline__ int cost_bucket(const SharedHead &sh, const int *xs, int Np, int j,
+                                           float dt) {
+    Lane<0> L;
+    L.xs = xs;
+    L.Np = Np;
+    L.j = j;
+    float a0 = 0.f;
+    for (int r = 0; r < sh.net.R; ++r)
+        a0 += sh.rate_f[r] * static_cast<float>(combos<0>(r, sh.net, L));
+    const float est = a0 * dt;
+    int b = 0;
+    if (est >= 1.f) b = min(15, ((__float_as_int(est) >> 23) & 0xFF) - 127 + 1);
+    return 15 - b;
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
@@ -251,7 +321,7 @@ __device__ void block_scan_u64(unsigned long long *q, int N, SharedHead &sh) {
 }
 
 // ------------------------------------------------------------------ kernels
-template <int RM>
+template <int RM, int UM>
 __global__ void __launch_bounds__(256, 2) filter_kernel(const FilterArgs args) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SharedHead sh;
@@ -281,7 +351,10 @@ __global__ void __launch_bounds__(256, 2) filter_kernel(const FilterArgs args) {
         for (int p = 0; p < P; ++p) ln = __dadd_rn(ln, log(args.net.sigma[p]));
         sh.lognorm = __dadd_rn(ln, __dmul_rn(0.5 * static_cast<double>(P), log(2.0 * M_PI)));
     }
-    if (tid < R) sh.rate[tid] = theta[args.net.rate_col[tid]];
+    if (tid < R) {
+        sh.rate[tid] = theta[args.net.rate_col[tid]];
+        sh.rate_f[tid] = static_cast<float>(theta[args.net.rate_col[tid]]);
+    }
     load_log_table(sh.logt);
     __syncthreads();
     if (!sh.valid) {
@@ -300,6 +373,7 @@ __global__ void __launch_bounds__(256, 2) filter_kernel(const FilterArgs args) {
     int *xs = reinterpret_cast<int *>(wbuf + N);                       // [U][N]
     int *xn = xs + U * Np;                                             // [U][N]
     int *anc = xn + U * Np;                                            // [N]
+    int *order = anc + N;                                              // [N] pool order
 
     for (int j = tid; j < N; j += B)
         for (int u = 0; u < U; ++u) xs[u * Np + j] = sh.net.x0[u];
@@ -343,9 +417,27 @@ __global__ void __launch_bounds__(256, 2) filter_kernel(const FilterArgs args) {
 
         const double t_k = args.obs_times[k];
         if (t_k > t_prev) {
-            if (tid == 0) sh.pool_next = 0;
+            // pool order: counting sort of the particles by expected work, heaviest first
+            const float dt = static_cast<float>(t_k - t_prev);
+            if (tid < 16) sh.bucket[tid] = 0;
             __syncthreads();
-            ssa_interval<RM>(sh, xs, Np, N, t_prev, t_k, key0, key1, lane, m32, args.budget, fired);
+            for (int j = tid; j < N; j += B) atomicAdd(&sh.bucket[cost_bucket(sh, xs, Np, j, dt)], 1);
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int b = 0; b < 16; ++b) {
+                    const int c = sh.bucket[b];
+                    sh.bucket[b] = run;
+                    run += c;
+                }
+                sh.pool_next = 0;
+            }
+            __syncthreads();
+            for (int j = tid; j < N; j += B)
+                order[atomicAdd(&sh.bucket[cost_bucket(sh, xs, Np, j, dt)], 1)] = j;
+            __syncthreads();
+            ssa_interval<RM, UM>(sh, xs, order, Np, N, t_prev, t_k, key0, key1, lane, m32,
+                                 args.budget, fired);
         }
         __syncthreads();
         if (sh.status != PF_ST_OK) break;
@@ -440,14 +532,14 @@ __global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t
     out[4 * i + 3] = w.w3;
 }
 
-template <int RM>
+template <int RM, int UM>
 int launch_tier(const FilterArgs &a, int B, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(filter_kernel<RM>,
+    cudaError_t e = cudaFuncSetAttribute(filter_kernel<RM, UM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     const int64_t F = a.M * a.T;
-    filter_kernel<RM><<<static_cast<unsigned>(F), B, smem, s>>>(a);
+    filter_kernel<RM, UM><<<static_cast<unsigned>(F), B, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -455,7 +547,7 @@ int launch_tier(const FilterArgs &a, int B, size_t smem, cudaStream_t s) {
 
 size_t filter_smem_bytes(int N, int U, int /*block_threads*/) {
     return static_cast<size_t>(N) * 8 + 2 * static_cast<size_t>(U) * N * 4 +
-           static_cast<size_t>(N) * 4 + 16;
+           2 * static_cast<size_t>(N) * 4 + 16;
 }
 
 int reaction_tier(int R) {
@@ -470,11 +562,12 @@ int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, v
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t smem = filter_smem_bytes(a.N, a.net.U, B);
     int e;
+    const bool small_u = a.net.U <= 4;
     switch (reaction_tier(a.net.R)) {
-        case 4: e = launch_tier<4>(a, B, smem, s); break;
-        case 8: e = launch_tier<8>(a, B, smem, s); break;
-        case 16: e = launch_tier<16>(a, B, smem, s); break;
-        default: e = launch_tier<32>(a, B, smem, s); break;
+        case 4: e = small_u ? launch_tier<4, 4>(a, B, smem, s) : launch_tier<4, 0>(a, B, smem, s); break;
+        case 8: e = small_u ? launch_tier<8, 4>(a, B, smem, s) : launch_tier<8, 0>(a, B, smem, s); break;
+        case 16: e = launch_tier<16, 0>(a, B, smem, s); break;
+        default: e = launch_tier<32, 0>(a, B, smem, s); break;
     }
     if (e != cudaSuccess) return e;
     const int rb = 128;
