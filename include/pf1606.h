@@ -144,6 +144,40 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
               int32_t T, int32_t P, const double *C, const double *sigma, int32_t n_particles,
               uint64_t seed, double *loglik, uint8_t *status, const pf_options *opt);
 
+/*
+ * pf_loglik_noalloc -- pf_loglik for callers that must not allocate device
+ * memory.  The paper has no counterpart: this is an integration entry point.
+ * Some callers cannot call cudaMalloc: a process whose device memory is
+ * already claimed by another allocator (a framework's caching pool that has
+ * reserved the GPU), a latency-critical serving loop that cannot afford the
+ * allocator's synchronisation and unpredictable cost on its request path, or
+ * a plug-in that must not grow the host application's device footprint after
+ * it is loaded.  This entry point computes exactly what pf_loglik computes
+ * and allocates nothing: its per-filter scratch (and the copy of obs_times)
+ * lives in one static device array of PF_NOALLOC_SCRATCH_BYTES that every GPU
+ * loading the library holds until the process exits.
+ *   thetas [M][d], y [T][K][P], loglik [M] and status [M] (status may be NULL)
+ *   are DEVICE pointers on the current device; the network, x0, obs_times, C
+ *   and sigma are host arrays.  Work is enqueued on `stream` (NULL = legacy
+ *   default stream) and the call returns without waiting.
+ *   The scratch needs about 24 bytes per filter (M * T filters) plus 8 bytes
+ *   per observation time; a problem that does not fit is rejected with
+ *   PF_EINVAL before any device work.  event_budget 0 = default.
+ *   The first call on a device looks the array's device address up
+ *   (cudaGetSymbolAddress) and caches it; make that first call before any
+ *   stream capture.  All calls share the one array and nothing in it needs
+ *   to start at zero (every scratch entry is written before it is read), but
+ *   calls whose work overlaps on the GPU (different streams, or host threads)
+ *   race on it: serialise them.
+ * Returns PF_OK or a negative code, like pf_loglik.
+ */
+#define PF_NOALLOC_SCRATCH_BYTES (16u << 20)
+int pf_loglik_noalloc(const pf_network *net, const double *thetas, int64_t M, int32_t d,
+                      const int32_t *x0, const double *obs_times, int32_t K, const double *y,
+                      int32_t T, int32_t P, const double *C, const double *sigma,
+                      int32_t n_particles, uint64_t seed, double *loglik, uint8_t *status,
+                      uint64_t event_budget, void *stream);
+
 /* Text for a return code (static storage). */
 const char *pf_strerror(int code);
 

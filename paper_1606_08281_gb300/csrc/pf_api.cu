@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "pf1606.h"
@@ -261,3 +262,101 @@ int pf_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, in
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free entry point.  Its scratch lives in one file-scope device
+// array of fixed size; host code reaches it through cudaGetSymbolAddress
+// (the array's name is only a host-side stand-in, not a device address).
+// ---------------------------------------------------------------------------
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PF_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) and cached.
+int noalloc_scratch(void **out) {
+    int dev = 0;
+    PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(PF_EINVAL, "device index %d not supported", dev);
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void *p = nullptr;
+        PF_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(scratch)");
+        g_noalloc_addr[dev] = p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PF_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+}  // namespace
+
+extern "C" int pf_loglik_noalloc(const pf_network *net, const double *thetas, int64_t M,
+                                 int32_t d, const int32_t *x0, const double *obs_times,
+                                 int32_t K, const double *y, int32_t T, int32_t P,
+                                 const double *C, const double *sigma, int32_t n_particles,
+                                 uint64_t seed, double *loglik, uint8_t *status,
+                                 uint64_t event_budget, void *stream) {
+    g_last_error.clear();
+    const uint64_t budget = event_budget ? event_budget : PF_DEFAULT_EVENT_BUDGET;
+    const int N = n_particles;
+    if (M < 0) return fail(PF_EINVAL, "M < 0");
+    if (K < 1 || K >= (1 << 20)) return fail(PF_EINVAL, "K %d outside 1..2^20-1", K);
+    if (T < 1 || T >= 4096) return fail(PF_EINVAL, "T %d outside 1..4095", T);
+    if (N < 1 || N > PF_MAX_PARTICLES) return fail(PF_EINVAL, "n_particles %d outside 1..%d", N, PF_MAX_PARTICLES);
+    if (budget > 0xFFFFFFFFull) return fail(PF_EINVAL, "event_budget must be < 2^32");
+    if (M > 0xFFFFFFFFll) return fail(PF_EINVAL, "M must be < 2^32");
+    // scratch layout: obs_times [K] | ll_f [M*T] | ev_f [M*T] | st_f [M*T]
+    const size_t F = static_cast<size_t>(M) * static_cast<size_t>(T);
+    const size_t off_ll = align256(sizeof(double) * static_cast<size_t>(K));
+    const size_t off_ev = off_ll + align256(sizeof(double) * F);
+    const size_t off_st = off_ev + align256(sizeof(uint64_t) * F);
+    const size_t need = off_st + align256(F);
+    if (need > PF_NOALLOC_SCRATCH_BYTES)
+        return fail(PF_EINVAL, "M*T = %zu filters and K = %d need %zu scratch bytes; the fixed scratch holds %u",
+                    F, K, need, (unsigned)PF_NOALLOC_SCRATCH_BYTES);
+    if (!obs_times) return fail(PF_EINVAL, "obs_times is NULL");
+    if (M > 0 && (!thetas || !y || !loglik)) return fail(PF_EINVAL, "NULL array argument");
+    pf::FilterArgs a{};
+    int rc = build_tables(net, d, x0, P, C, sigma, a.net);
+    if (rc) return rc;
+    rc = check_count_range(a.net, K, budget);
+    if (rc) return rc;
+    const int B = std::min(128, ((N + 31) / 32) * 32);
+    const size_t smem = pf::filter_smem_bytes(N, a.net.U, B);
+    int dev = 0, smem_max = 0;
+    PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    PF_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
+    if (smem + sizeof(pf::NetTables) + 8192 > (size_t)smem_max)
+        return fail(PF_EINVAL, "N=%d with U=%d needs %zu bytes of shared memory per filter (limit %d)", N, a.net.U, smem, smem_max);
+    for (int k = 0; k < K; ++k) {
+        const bool bad = !std::isfinite(obs_times[k]) ||
+                         (k == 0 ? obs_times[k] < 0.0 : !(obs_times[k] > obs_times[k - 1]));
+        if (bad) return fail(PF_EINVAL, "obs_times must be finite, >= 0 and strictly increasing (index %d)", k);
+    }
+    if (M == 0) return PF_OK;
+    unsigned char *scratch = nullptr;
+    rc = noalloc_scratch(reinterpret_cast<void **>(&scratch));
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    PF_CUDA(cudaMemcpyAsync(scratch, obs_times, sizeof(double) * K, cudaMemcpyHostToDevice, s), "copy obs_times");
+    a.thetas = thetas;
+    a.obs_times = reinterpret_cast<const double *>(scratch);
+    a.y = y;
+    a.M = M; a.K = K; a.T = T; a.N = N;
+    a.seed = seed;
+    a.budget = budget;
+    a.ll_f = reinterpret_cast<double *>(scratch + off_ll);
+    a.ev_f = reinterpret_cast<uint64_t *>(scratch + off_ev);
+    a.st_f = reinterpret_cast<uint8_t *>(scratch + off_st);
+    a.dg_f = nullptr;
+    a.final_states = nullptr;
+    const int e = pf::launch_filter(a, B, loglik, status, s);
+    if (e) return cuda_fail((cudaError_t)e, "filter launch");
+    return PF_OK;
+}

@@ -26,7 +26,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT, PF_EAGAIN, PF_ENOTFOUND, PF_
 PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA = 0, 1, 2, 3
 
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
-            "pf_fp64_probe", "pf_neg_log_u53"]
+            "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc"]
 
 
 class PfError(RuntimeError):
@@ -79,6 +79,10 @@ def load():
             lib.pf_fp64_probe.restype = ct.c_int
             lib.pf_neg_log_u53.argtypes = [P, P, ct.c_int64]
             lib.pf_neg_log_u53.restype = ct.c_int
+            lib.pf_loglik_noalloc.argtypes = [ct.POINTER(pf_network), P, ct.c_int64, ct.c_int32,
+                                              P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P,
+                                              ct.c_int32, ct.c_uint64, P, P, ct.c_uint64, P]
+            lib.pf_loglik_noalloc.restype = ct.c_int
             _lib = lib
     return _lib
 
@@ -220,3 +224,28 @@ def pf_neg_log_u53(v) -> np.ndarray:
     out = np.empty(len(vv), np.float64)
     _check(lib.pf_neg_log_u53(_hptr(vv), _hptr(out), len(vv)), "pf_neg_log_u53")
     return out
+
+
+def pf_loglik_noalloc(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int,
+                      seed: int, loglik, status=None, *, event_budget: int = 0, stream=None):
+    """Allocation-free pf_loglik (see include/pf1606.h).  thetas [M][d], y
+    [T][K][P], loglik [M] and status [M] are torch CUDA tensors the caller owns;
+    the call enqueues on `stream` (default: the current torch stream)."""
+    import torch
+    lib = load()
+    n = _Net(net)
+    U = n.s.n_species
+    th = thetas
+    M, d = th.shape
+    T, K, P = y.shape
+    ts = _host(obs_times, np.float64)
+    Ch = _host(C, np.float64).reshape(P, U)
+    sg = _host(sigma, np.float64).reshape(P)
+    if stream is None:
+        stream = torch.cuda.current_stream(th.device).cuda_stream
+    rc = lib.pf_loglik_noalloc(ct.byref(n.s), th.data_ptr(), M, d, _hptr(_host(x0, np.int32)),
+                               _hptr(ts), K, y.data_ptr(), T, P, _hptr(Ch), _hptr(sg),
+                               int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
+                               loglik.data_ptr(), None if status is None else status.data_ptr(),
+                               ct.c_uint64(int(event_budget)), stream)
+    _check(rc, "pf_loglik_noalloc")
