@@ -105,8 +105,16 @@ typedef struct {
  *                 resampling / simulation history, used to compare paths.
  *   final_states  optional [M][T][N][U] particle states after the last
  *                 interval (int32).
+ *   schedule      launch order of the filters: PF_SCHED_AUTO (heaviest-first
+ *                 when the batch spans several waves of the GPU),
+ *                 PF_SCHED_NATURAL (row order), PF_SCHED_HEAVY_FIRST (a pilot
+ *                 path per theta row estimates its cost; rows run heaviest
+ *                 first).  Results never depend on the order.
  *   Diagnostics are defined only for filters whose status is PF_ST_OK.
  */
+#define PF_SCHED_AUTO 0
+#define PF_SCHED_NATURAL 1
+#define PF_SCHED_HEAVY_FIRST 2
 typedef struct {
     uint64_t event_budget;
     int32_t device_ptrs;
@@ -116,6 +124,8 @@ typedef struct {
     uint64_t *events;
     uint64_t *digest;
     int32_t *final_states;
+    int32_t schedule;
+    int32_t reserved;
 } pf_options;
 
 /*

@@ -228,6 +228,17 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     if (o.digest) { PF_CUDA(pick(o.digest, b_dgf, sizeof(uint64_t) * F, &p), "alloc digest"); a.dg_f = (uint64_t *)p; }
     if (o.final_states) { PF_CUDA(pick(o.final_states, b_fs, n_fs, &p), "alloc final_states"); a.final_states = (int32_t *)p; }
 
+    DevBuf b_cost, b_order;
+    const bool heavy_first = o.schedule == PF_SCHED_HEAVY_FIRST ||
+                             (o.schedule == PF_SCHED_AUTO && F >= 2048);
+    if (o.schedule < 0 || o.schedule > PF_SCHED_HEAVY_FIRST) return fail(PF_EINVAL, "unknown schedule %d", o.schedule);
+    if (heavy_first) {
+        PF_CUDA(b_cost.alloc(sizeof(uint32_t) * M, s), "alloc schedule");
+        PF_CUDA(b_order.alloc(sizeof(uint32_t) * M, s), "alloc schedule");
+        int e = pf::launch_schedule(a, (uint32_t *)b_cost.p, (uint32_t *)b_order.p, 1u << 16, s);
+        if (e) return cuda_fail((cudaError_t)e, "schedule launch");
+        a.row_order = (const uint32_t *)b_order.p;
+    }
     int e = pf::launch_filter(a, B, d_ll, d_st, s);
     if (e) return cuda_fail((cudaError_t)e, "filter launch");
 

@@ -327,9 +327,11 @@ __global__ void __launch_bounds__(256, 2) filter_kernel(const FilterArgs args) {
     __shared__ SharedHead sh;
     const int tid = threadIdx.x, B = blockDim.x;
     const int T = args.T, N = args.N, K = args.K;
-    const int64_t f = blockIdx.x;
-    const int64_t mrow = f / T;
-    const int traj = static_cast<int>(f - mrow * T);
+    const int64_t slot = blockIdx.x;
+    int64_t mrow = slot / T;
+    const int traj = static_cast<int>(slot - mrow * T);
+    if (args.row_order) mrow = args.row_order[mrow];
+    const int64_t f = mrow * T + traj;
 
     {  // network tables -> shared memory
         const uint32_t *src = reinterpret_cast<const uint32_t *>(&args.net);
@@ -521,6 +523,105 @@ __global__ void reduce_kernel(const double *ll_f, const uint8_t *st_f, int64_t M
     if (status) status[m] = static_cast<uint8_t>(st);
 }
 
+// One unconditioned direct-method path per theta row over [0, t_K], counting
+// events (at most `cap`): a cost estimate for scheduling only.  Its random
+// stream (particle lane 0xFFFFFFFE, interval word 0xFFFFFFFF) is disjoint from
+// the filters' streams.
+template <int RM>
+__global__ void __launch_bounds__(128) pilot_kernel(const FilterArgs args, uint32_t *cost,
+                                                    uint32_t cap) {
+    __shared__ NetTables net;
+    __shared__ LogTab logt;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&args.net);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&net);
+        for (int i = threadIdx.x; i < static_cast<int>(sizeof(NetTables) / 4); i += blockDim.x)
+            dst[i] = src[i];
+    }
+    load_log_table(logt);
+    __syncthreads();
+    const int64_t m = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (m >= args.M) return;
+    const int R = net.R, U = net.U, d = net.d;
+    const double *theta = args.thetas + m * d;
+    bool ok = true;
+    for (int c = 0; c < d; ++c) ok = ok && isfinite(theta[c]) && theta[c] >= 0.0;
+    if (!ok) {
+        cost[m] = 0;
+        return;
+    }
+    double rate[RM];
+#pragma unroll
+    for (int r = 0; r < RM; ++r) rate[r] = r < R ? theta[net.rate_col[r]] : 0.0;
+    int x[PF_MAX_SPECIES];
+    for (int u = 0; u < PF_MAX_SPECIES; ++u) x[u] = u < U ? net.x0[u] : 0;
+    const uint32_t key0 = static_cast<uint32_t>(args.seed);
+    const uint32_t key1 = static_cast<uint32_t>(args.seed >> 32);
+    const long long t_end_bits = __double_as_longlong(args.obs_times[args.K - 1]);
+    double t = 0.0;
+    uint32_t events = 0;
+    while (events < cap) {
+        double a[RM], S[RM], run = 0.0;
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            long long h = 1;
+            if (r < R) {
+                if (net.sp_a[r] >= 0) h = binom_small(x[net.sp_a[r]], net.ord_a[r]);
+                if (net.sp_b[r] >= 0) h *= binom_small(x[net.sp_b[r]], net.ord_b[r]);
+            }
+            a[r] = r < R ? __dmul_rn(rate[r], count_to_double(h)) : 0.0;
+            run = r == 0 ? a[0] : __dadd_rn(run, a[r]);
+            S[r] = run;
+        }
+        if (__double_as_longlong(run) == 0) break;
+        const Philox4 w = philox4x32_10(events, 0xFFFFFFFEu, 0xFFFFFFFFu, static_cast<uint32_t>(m),
+                                        key0, key1);
+        const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+        const uint64_t v2 = ((static_cast<uint64_t>(w.w3) << 32) | w.w2) >> 11;
+        t = __dadd_rn(t, __ddiv_rn(neg_log_u53((r0 >> 11) + 1ull, logt), run));
+        if (__double_as_longlong(t) > t_end_bits) break;
+        const long long tb = __double_as_longlong(__dmul_rn(v2 ? scaled_u53(v2) : 0.0, run));
+        int chosen = 0;
+#pragma unroll
+        for (int r = 0; r < RM; ++r) chosen += (r < R && __double_as_longlong(S[r]) <= tb) ? 1 : 0;
+        if (chosen >= R) {
+            chosen = 0;
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+                if (r < R && __double_as_longlong(a[r]) != 0) chosen = r;
+        }
+        for (int i = 0; i < net.n_change[chosen]; ++i) x[net.ch_sp[chosen][i]] += net.ch_delta[chosen][i];
+        ++events;
+    }
+    cost[m] = events;
+}
+
+// Counting sort of theta rows by pilot cost, heaviest first (4 buckets per
+// octave).  One block.
+__global__ void __launch_bounds__(1024) order_kernel(const uint32_t *cost, int64_t M,
+                                                      uint32_t *order) {
+    __shared__ int hist[64];
+    auto bucket = [](uint32_t c) {
+        const int lg = c == 0 ? 0 : static_cast<int>(4.0f * __log2f(static_cast<float>(c)));
+        return 63 - min(63, max(0, lg));
+    };
+    if (threadIdx.x < 64) hist[threadIdx.x] = 0;
+    __syncthreads();
+    for (int64_t m = threadIdx.x; m < M; m += blockDim.x) atomicAdd(&hist[bucket(cost[m])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int b = 0; b < 64; ++b) {
+            const int c = hist[b];
+            hist[b] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    for (int64_t m = threadIdx.x; m < M; m += blockDim.x)
+        order[atomicAdd(&hist[bucket(cost[m])], 1)] = static_cast<uint32_t>(m);
+}
+
 __global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -573,6 +674,23 @@ int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, v
     const int rb = 128;
     reduce_kernel<<<static_cast<unsigned>((a.M + rb - 1) / rb), rb, 0, s>>>(a.ll_f, a.st_f, a.M,
                                                                            a.T, loglik, status);
+    return cudaGetLastError();
+}
+
+int launch_schedule(const FilterArgs &a, uint32_t *cost, uint32_t *order, uint32_t cap,
+                    void *stream) {
+    if (a.M == 0) return cudaSuccess;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const unsigned g = static_cast<unsigned>((a.M + 127) / 128);
+    switch (reaction_tier(a.net.R)) {
+        case 4: pilot_kernel<4><<<g, 128, 0, s>>>(a, cost, cap); break;
+        case 8: pilot_kernel<8><<<g, 128, 0, s>>>(a, cost, cap); break;
+        case 16: pilot_kernel<16><<<g, 128, 0, s>>>(a, cost, cap); break;
+        default: pilot_kernel<32><<<g, 128, 0, s>>>(a, cost, cap); break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    order_kernel<<<1, 1024, 0, s>>>(cost, a.M, order);
     return cudaGetLastError();
 }
 

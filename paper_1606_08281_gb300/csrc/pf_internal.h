@@ -41,6 +41,7 @@ struct FilterArgs {
     uint64_t *ev_f;
     uint64_t *dg_f;          // may be null: digest not computed
     int32_t *final_states;   // [M*T][N][U], may be null
+    const uint32_t *row_order;  // [M] theta rows in launch order (null: 0..M-1)
 };
 
 // Bytes of dynamic shared memory the filter kernel needs for N particles.
@@ -53,6 +54,14 @@ int reaction_tier(int R);
 // Returns a cudaError_t value (0 on success).
 int launch_filter(const FilterArgs &a, int block_threads, double *loglik, uint8_t *status,
                   void *stream);
+
+// Heaviest-first launch order of the theta rows: a pilot kernel simulates
+// one unconditioned path per row over [0, t_K] (its own random stream, at most
+// `cap` events) and a one-block counting sort orders rows by that event count.
+// cost [M] and order [M] are caller-provided device buffers.  The order only
+// affects scheduling, never results.
+int launch_schedule(const FilterArgs &a, uint32_t *cost, uint32_t *order, uint32_t cap,
+                    void *stream);
 
 int launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                   void *stream);

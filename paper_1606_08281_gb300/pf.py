@@ -24,6 +24,7 @@ _lock = threading.Lock()
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT, PF_EAGAIN, PF_ENOTFOUND, PF_EBUSY = (
     0, -1, -2, -3, -4, -5, -6, -7)
 PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA = 0, 1, 2, 3
+PF_SCHED_AUTO, PF_SCHED_NATURAL, PF_SCHED_HEAVY_FIRST = 0, 1, 2
 
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc"]
@@ -45,7 +46,7 @@ class pf_options(ct.Structure):
     _fields_ = [("event_budget", ct.c_uint64), ("device_ptrs", ct.c_int32),
                 ("block_threads", ct.c_int32), ("stream", ct.c_void_p),
                 ("ll_traj", ct.c_void_p), ("events", ct.c_void_p), ("digest", ct.c_void_p),
-                ("final_states", ct.c_void_p)]
+                ("final_states", ct.c_void_p), ("schedule", ct.c_int32), ("reserved", ct.c_int32)]
 
 
 def library_path() -> Path:
@@ -131,7 +132,8 @@ def _is_torch_cuda(x) -> bool:
 
 def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, seed: int, *,
               event_budget: int = 0, block_threads: int = 0, stream=None,
-              diagnostics: bool = False, final_states: bool = False, out=None):
+              diagnostics: bool = False, final_states: bool = False, out=None,
+              schedule: int = PF_SCHED_AUTO):
     """Log-likelihood of every theta row (see pf_loglik in include/pf1606.h).
 
     Returns a dict with 'loglik' [M] and 'status' [M]; with diagnostics=True
@@ -189,7 +191,7 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
     sg = _host(sigma, np.float64).reshape(P)
     opt = pf_options(int(event_budget), 1 if device else 0, int(block_threads),
                      stream if device else None, ptr("ll_traj"), ptr("events"), ptr("digest"),
-                     ptr("final_states"))
+                     ptr("final_states"), int(schedule), 0)
     rc = lib.pf_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), p_ts, K, p_y, T, P, _hptr(Ch),
                        _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
                        ptr("loglik"), ptr("status"), ct.byref(opt))

@@ -175,6 +175,18 @@ def test_device_pointer_mode_matches_host_mode(pf):
     assert (d["digest"].cpu().numpy().view(np.uint64) == h["digest"]).all()
 
 
+def test_schedule_does_not_change_results(pf):
+    """Natural and heaviest-first launch orders give identical results."""
+    w = W.gene_expression().subset(T=4, K=8)
+    th = w.thetas(600)                          # 2400 filters: several waves
+    a = pf.pf_loglik(w.net, th, w.x0, w.obs_times, w.observations(), w.C, w.sigma, 64, 5,
+                     diagnostics=True, schedule=pf.PF_SCHED_NATURAL)
+    b = pf.pf_loglik(w.net, th, w.x0, w.obs_times, w.observations(), w.C, w.sigma, 64, 5,
+                     diagnostics=True, schedule=pf.PF_SCHED_HEAVY_FIRST)
+    assert (a["loglik"] == b["loglik"]).all() and (a["digest"] == b["digest"]).all()
+    assert (a["events"] == b["events"]).all()
+
+
 def test_repeatable(pf):
     w = W.gene_expression().subset(T=2, K=10)
     a = pf.pf_loglik(w.net, w.thetas(32), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
