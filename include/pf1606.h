@@ -110,6 +110,9 @@ typedef struct {
  *                 PF_SCHED_NATURAL (row order), PF_SCHED_HEAVY_FIRST (a pilot
  *                 path per theta row estimates its cost; rows run heaviest
  *                 first).  Results never depend on the order.
+ *   row_order     optional [M] permutation of 0..M-1 (same memory space as
+ *                 thetas): the theta rows in the order their filters are
+ *                 launched; overrides `schedule`.
  *   Diagnostics are defined only for filters whose status is PF_ST_OK.
  */
 #define PF_SCHED_AUTO 0
@@ -126,6 +129,7 @@ typedef struct {
     int32_t *final_states;
     int32_t schedule;
     int32_t reserved;
+    const uint32_t *row_order;
 } pf_options;
 
 /*

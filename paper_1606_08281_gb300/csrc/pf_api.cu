@@ -229,8 +229,17 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     if (o.final_states) { PF_CUDA(pick(o.final_states, b_fs, n_fs, &p), "alloc final_states"); a.final_states = (int32_t *)p; }
 
     DevBuf b_cost, b_order;
-    const bool heavy_first = o.schedule == PF_SCHED_HEAVY_FIRST ||
-                             (o.schedule == PF_SCHED_AUTO && F >= 2048);
+    const bool heavy_first = !o.row_order && (o.schedule == PF_SCHED_HEAVY_FIRST ||
+                                              (o.schedule == PF_SCHED_AUTO && F >= 2048));
+    if (o.row_order) {
+        if (o.device_ptrs) {
+            a.row_order = o.row_order;
+        } else {
+            PF_CUDA(b_order.alloc(sizeof(uint32_t) * M, s), "alloc row order");
+            PF_CUDA(cudaMemcpyAsync(b_order.p, o.row_order, sizeof(uint32_t) * M, cudaMemcpyHostToDevice, s), "copy row order");
+            a.row_order = (const uint32_t *)b_order.p;
+        }
+    }
     if (o.schedule < 0 || o.schedule > PF_SCHED_HEAVY_FIRST) return fail(PF_EINVAL, "unknown schedule %d", o.schedule);
     if (heavy_first) {
         PF_CUDA(b_cost.alloc(sizeof(uint32_t) * M, s), "alloc schedule");

@@ -46,7 +46,8 @@ class pf_options(ct.Structure):
     _fields_ = [("event_budget", ct.c_uint64), ("device_ptrs", ct.c_int32),
                 ("block_threads", ct.c_int32), ("stream", ct.c_void_p),
                 ("ll_traj", ct.c_void_p), ("events", ct.c_void_p), ("digest", ct.c_void_p),
-                ("final_states", ct.c_void_p), ("schedule", ct.c_int32), ("reserved", ct.c_int32)]
+                ("final_states", ct.c_void_p), ("schedule", ct.c_int32), ("reserved", ct.c_int32),
+                ("row_order", ct.c_void_p)]
 
 
 def library_path() -> Path:
@@ -133,7 +134,7 @@ def _is_torch_cuda(x) -> bool:
 def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, seed: int, *,
               event_budget: int = 0, block_threads: int = 0, stream=None,
               diagnostics: bool = False, final_states: bool = False, out=None,
-              schedule: int = PF_SCHED_AUTO):
+              schedule: int = PF_SCHED_AUTO, row_order=None):
     """Log-likelihood of every theta row (see pf_loglik in include/pf1606.h).
 
     Returns a dict with 'loglik' [M] and 'status' [M]; with diagnostics=True
@@ -189,9 +190,17 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
         p_th, p_ts, p_y = _hptr(th), _hptr(ts), _hptr(yy)
     Ch = _host(C, np.float64).reshape(P, U)
     sg = _host(sigma, np.float64).reshape(P)
+    if row_order is None:
+        p_ro = None
+    elif device:
+        ro = row_order.contiguous()
+        p_ro = ro.data_ptr()
+    else:
+        ro = _host(row_order, np.uint32)
+        p_ro = _hptr(ro)
     opt = pf_options(int(event_budget), 1 if device else 0, int(block_threads),
                      stream if device else None, ptr("ll_traj"), ptr("events"), ptr("digest"),
-                     ptr("final_states"), int(schedule), 0)
+                     ptr("final_states"), int(schedule), 0, p_ro)
     rc = lib.pf_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), p_ts, K, p_y, T, P, _hptr(Ch),
                        _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
                        ptr("loglik"), ptr("status"), ct.byref(opt))
