@@ -105,11 +105,10 @@ typedef struct {
  *                 resampling / simulation history, used to compare paths.
  *   final_states  optional [M][T][N][U] particle states after the last
  *                 interval (int32).
- *   schedule      launch order of the filters: PF_SCHED_AUTO (heaviest-first
- *                 when the batch spans several waves of the GPU),
- *                 PF_SCHED_NATURAL (row order), PF_SCHED_HEAVY_FIRST (a pilot
- *                 path per theta row estimates its cost; rows run heaviest
- *                 first).  Results never depend on the order.
+ *   schedule      launch order of the filters: PF_SCHED_AUTO (currently row
+ *                 order), PF_SCHED_NATURAL (row order), PF_SCHED_HEAVY_FIRST (a
+ *                 pilot path per theta row estimates its cost; rows run
+ *                 heaviest first).  Results never depend on the order.
  *   row_order     optional [M] permutation of 0..M-1 (same memory space as
  *                 thetas): the theta rows in the order their filters are
  *                 launched; overrides `schedule`.

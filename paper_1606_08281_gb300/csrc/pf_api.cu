@@ -229,8 +229,9 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     if (o.final_states) { PF_CUDA(pick(o.final_states, b_fs, n_fs, &p), "alloc final_states"); a.final_states = (int32_t *)p; }
 
     DevBuf b_cost, b_order;
-    const bool heavy_first = !o.row_order && (o.schedule == PF_SCHED_HEAVY_FIRST ||
-                                              (o.schedule == PF_SCHED_AUTO && F >= 2048));
+    // AUTO keeps row order: on a uniform-prior batch an unconditioned pilot path
+    // predicts filter cost too loosely for heaviest-first to pay off.
+    const bool heavy_first = !o.row_order && o.schedule == PF_SCHED_HEAVY_FIRST;
     if (o.row_order) {
         if (o.device_ptrs) {
             a.row_order = o.row_order;
