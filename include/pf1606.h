@@ -191,6 +191,97 @@ int pf_loglik_noalloc(const pf_network *net, const double *thetas, int64_t M, in
                       int32_t n_particles, uint64_t seed, double *loglik, uint8_t *status,
                       uint64_t event_budget, void *stream);
 
+/* ======================================================================
+ * Batching and serving.
+ *
+ * The level-set sampler (Alg. 2, "LNS") sends batches of candidate theta
+ * whose likelihood must be estimated (its parallel part, Alg. 1).  A
+ * context keeps problems (network + observed trajectories) resident on the
+ * device and evaluates requests -- (problem, theta rows, N, K, seed) -- in
+ * persistent kernels fed by a device work list of filters, replayed from a
+ * CUDA graph captured once per slot.  Requests that differ in problem,
+ * theta count, particle count and number of observation times share one
+ * launch.  A request's results depend only on its own inputs (the random
+ * stream is keyed by the request's seed and its local theta index), never on
+ * what else is in the batch.
+ * ====================================================================== */
+typedef struct pf_ctx pf_ctx;
+
+/*
+ * pf_ctx_create -- new context on the current device.
+ *   mem_budget_bytes  device+pinned bytes that admitted, unfinished requests
+ *                     may hold at once (theta, outputs, per-filter scratch);
+ *                     0 = 1 GiB.  A request larger than the whole budget is
+ *                     refused with PF_EBUSY at submission.
+ *   n_slots           batches that may be in flight at once (1..8; 0 = 3):
+ *                     each slot owns its tables, stream and captured graph.
+ *   max_particles     largest N a request may use (0 = 4096).
+ * Allocates all slot memory up front.  Returns PF_OK, PF_EINVAL, PF_ENOMEM or
+ * PF_ECUDA.
+ */
+int pf_ctx_create(pf_ctx **ctx, size_t mem_budget_bytes, int32_t n_slots, int32_t max_particles);
+
+/*
+ * pf_ctx_load_problem -- copy a problem to the device (Sec. "General Task":
+ * network, x0, observation times, T observed trajectories y [T][K][P],
+ * C [P][U], sigma [P]); host pointers, same rules as pf_loglik.  Writes its
+ * id to *problem_id.
+ */
+int pf_ctx_load_problem(pf_ctx *ctx, const pf_network *net, int32_t d, const int32_t *x0,
+                        const double *obs_times, int32_t K, const double *y, int32_t T,
+                        int32_t P, const double *C, const double *sigma, int32_t *problem_id);
+
+/* One request: host arrays, read at submission (theta) and written at
+ * completion (loglik/status; status may be NULL).  K_use = number of leading
+ * observation times to use (0 = all of the problem's).  event_budget 0 =
+ * default.  loglik_threshold is carried for the caller's bookkeeping (the
+ * level-set threshold epsilon_k of Alg. 2); it does not change the result. */
+typedef struct {
+    int32_t problem_id;
+    int32_t d;
+    const double *thetas;  /* [M][d] */
+    int64_t M;
+    int32_t n_particles;
+    int32_t K_use;
+    uint64_t seed;
+    uint64_t event_budget;
+    double loglik_threshold;
+    double *loglik;        /* [M] out */
+    uint8_t *status;       /* [M] out, may be NULL */
+} pf_request;
+
+/*
+ * pf_ctx_run_batch -- evaluate n requests together in one replay of a slot's
+ * graph and wait for them.  Fails with PF_EBUSY if they exceed one slot's
+ * capacity; use pf_submit for streams of requests.
+ */
+int pf_ctx_run_batch(pf_ctx *ctx, const pf_request *reqs, int32_t n);
+
+/*
+ * pf_submit -- queue one request for serving and return at once with its id.
+ * A worker thread admits queued requests in arrival order while their memory
+ * footprint fits the budget and a slot is free, gathers them into one batch,
+ * and launches it while earlier batches may still run on other slots
+ * (continuous batching).  The request's host arrays must stay valid until
+ * pf_poll reports completion.
+ */
+int pf_submit(pf_ctx *ctx, const pf_request *req, int64_t *req_id);
+
+/*
+ * pf_poll -- PF_OK when request req_id has finished (its loglik/status arrays
+ * are written; the id is then forgotten), PF_EAGAIN while it is queued or
+ * running, PF_ENOTFOUND for an unknown id.  If wait_ms > 0 the call blocks up
+ * to that long.  t_submit / t_done (may be NULL) receive the submission and
+ * completion times in seconds on the context's steady clock.
+ */
+int pf_poll(pf_ctx *ctx, int64_t req_id, int32_t wait_ms, double *t_submit, double *t_done);
+
+/* pf_ctx_stats -- batches launched, requests done, filters run (any NULL). */
+int pf_ctx_stats(pf_ctx *ctx, int64_t *batches, int64_t *requests, int64_t *filters);
+
+/* pf_ctx_destroy -- wait for in-flight work, stop the worker, free everything. */
+int pf_ctx_destroy(pf_ctx *ctx);
+
 /* Text for a return code (static storage). */
 const char *pf_strerror(int code);
 

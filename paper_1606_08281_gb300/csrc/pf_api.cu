@@ -16,8 +16,10 @@
 #include "pf_internal.h"
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace pf {
 
 int fail(int code, const char *fmt, ...) {
     char buf[512];
@@ -29,7 +31,8 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
-int cuda_fail(cudaError_t e, const char *what) {
+int cuda_fail(int err, const char *what) {
+    const cudaError_t e = static_cast<cudaError_t>(err);
     if (e == cudaErrorMemoryAllocation) return fail(PF_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
     return fail(PF_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
@@ -39,6 +42,8 @@ int cuda_fail(cudaError_t e, const char *what) {
         cudaError_t e_ = (call);                              \
         if (e_ != cudaSuccess) return cuda_fail(e_, what);    \
     } while (0)
+
+void clear_error() { g_last_error.clear(); }
 
 // Build the kernels' network tables from the caller's description.
 int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P, const double *C,
@@ -114,6 +119,23 @@ int check_count_range(const pf::NetTables &t, int K, uint64_t budget) {
         return fail(PF_EINVAL, "x0 + K * event_budget * max gain (%.3g) could overflow int32 counts; lower event_budget", worst);
     return PF_OK;
 }
+
+int check_obs_times(const double *obs_times, int K) {
+    for (int k = 0; k < K; ++k) {
+        const bool bad = !std::isfinite(obs_times[k]) ||
+                         (k == 0 ? obs_times[k] < 0.0 : !(obs_times[k] > obs_times[k - 1]));
+        if (bad) return fail(PF_EINVAL, "obs_times must be finite, >= 0 and strictly increasing (index %d)", k);
+    }
+    return PF_OK;
+}
+
+}  // namespace pf
+
+namespace {
+using pf::fail;
+using pf::cuda_fail;
+using pf::build_tables;
+using pf::check_count_range;
 
 struct DevBuf {
     void *p = nullptr;

@@ -1,0 +1,520 @@
+// Device code of the particle filter, shared by the plain launch
+// (pf_filter.cu) and the persistent batch kernels (pf_batch.cu).
+//
+// One thread block runs one filter at a time, i.e. one (theta row, observed trajectory)
+// pair, through all K observation times (Supp. I, algorithm "Likelihood
+// Approximation using particle filter"):
+//   resample by the previous weights -> simulate every particle to t_k with
+//   the direct-method SSA -> Gaussian weight -> log-sum-exp increment.
+// Within one interval the particles form a pool: each lane simulates one
+// particle and, when that particle reaches t_k, takes the next unclaimed one
+// (a shared-memory counter), so warps stay full although particles fire very
+// different numbers of reactions.  GB300's FP64 pipe spends the same 16
+// cycles on a warp instruction whatever its active-lane count, so idle lanes
+// would cost FP64 throughput directly.
+// The whole particle population lives in shared memory: states int32 [U][N]
+// (two buffers for the gather), the weights / integer-weight prefix sums
+// (8 bytes per particle, reused), and the ancestor indices.  Nothing of the
+// filter touches HBM between its first load and its final store.
+//
+// Arithmetic that decides integer outcomes (propensities, their prefix sums,
+// event times, the Gaussian exponent) uses explicit round-to-nearest
+// intrinsics so that the compiler cannot fuse a multiply and an add; the
+// results then match a plain sequential FP64 restatement bit for bit, except
+// where CUDA's log/exp differ from another libm in the last place.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "fastmath.cuh"
+#include "pf_internal.h"
+#include "philox.cuh"
+
+namespace pf {
+namespace dev {
+
+
+constexpr int kMaxWarps = 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+constexpr uint32_t kResampleLane = 0xFFFFFFFFu;
+
+struct SharedHead {
+    NetTables net;
+    double rate[PF_MAX_REACTIONS];   // theta[rate_col[r]] of this filter's row
+    double red_d[kMaxWarps];
+    unsigned long long red_u[kMaxWarps];
+    double bcast_d;
+    unsigned long long u_off;
+    double ll;
+    double lognorm;
+    int status;
+    int valid;
+    int pool_next;
+    int bucket[16];
+    float rate_f[PF_MAX_REACTIONS];  // FP32 copy of rate[], for cost estimates only
+    LogTab logt;
+};
+
+// ------------------------------------------------------------------ helpers
+__device__ __forceinline__ long long binom_small(int x, int p) {
+    const long long xl = x;
+    if (p == 0) return 1;
+    if (p == 1) return xl;
+    return x >= 2 ? (xl * (xl - 1)) / 2 : 0;  // p == 2
+}
+
+// Particle state of the lane's current particle: in registers when the
+// network has at most UM species (UM > 0), else read in place from shared
+// memory (UM == 0).
+template <int UM>
+struct Lane {
+    int x[UM > 0 ? UM : 1];
+    const int *xs;
+    int Np, j;
+    __device__ __forceinline__ int get(int sp) const {
+        if constexpr (UM > 0) {
+            int v = x[0];
+#pragma unroll
+            for (int u = 1; u < UM; ++u) v = (sp == u) ? x[u] : v;
+            return v;
+        } else {
+            return xs[sp * Np + j];
+        }
+    }
+};
+
+// h_r(x) = prod_u binom(x_u, p_ru)  (mass action, Sec. "Chemical Reaction Networks")
+template <int UM>
+__device__ __forceinline__ long long combos(int r, const NetTables &n, const Lane<UM> &L) {
+    long long h = 1;
+    const int sa = n.sp_a[r];
+    if (sa >= 0) h = binom_small(L.get(sa), n.ord_a[r]);
+    const int sb = n.sp_b[r];
+    if (sb >= 0) h *= binom_small(L.get(sb), n.ord_b[r]);
+    return h;
+}
+
+// a_r = theta_rho(r) * h_r(x)
+template <int UM>
+__device__ __forceinline__ double propensity(int r, const SharedHead &sh, const Lane<UM> &L) {
+    return __dmul_rn(sh.rate[r], count_to_double(combos<UM>(r, sh.net, L)));
+}
+
+// Bits of a non-negative double: for x, y >= +0, x <= y iff bits(x) <= bits(y)
+// as signed integers, so these compares run on the integer pipes.
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+
+// Simulate every particle of the filter from t_prev to t_end by Gillespie's
+// direct method (Supp. I, "Simulate X_t"; Sec. "The stochastic birth-death
+// Model": SSA).  Lanes take particles from a pool in the order `order`
+// (heaviest expected work first); each loop trip is one direct-method step of
+// every active lane.  Failure is reported through sh.status (PF_ST_BUDGET when
+// a particle needed more than `budget` draws); `fired` counts reactions.
+template <int RM, int UM>
+__device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, int N,
+                             double t_prev, double t_end, uint32_t key0, uint32_t key1,
+                             uint32_t lane, uint32_t mrow, uint64_t budget,
+                             unsigned long long &fired) {
+    const int R = sh.net.R, U = sh.net.U;
+    const uint32_t all = (R >= 32) ? 0xFFFFFFFFu : ((1u << R) - 1u);
+    const long long t_end_bits = dbits(t_end);
+    Lane<UM> L;
+    L.xs = xs;
+    L.Np = Np;
+    auto take = [&](bool &act) {
+        const int slot = atomicAdd(&sh.pool_next, 1);
+        act = slot < N;
+        L.j = act ? order[slot] : 0;
+        if constexpr (UM > 0) {
+#pragma unroll
+            for (int u = 0; u < UM; ++u) L.x[u] = (act && u < U) ? xs[u * Np + L.j] : 0;
+        }
+    };
+    double a[RM], S[RM];
+#pragma unroll
+    for (int r = 0; r < RM; ++r) a[r] = 0.0;
+    bool active;
+    take(active);
+    double t = t_prev;
+    uint32_t draws = 0;
+    uint32_t mask = all;  // propensities to (re)compute before the next step
+    while (__any_sync(kFull, active)) {
+        if (!active) continue;
+#pragma unroll
+        for (int r = 0; r < RM; ++r)
+            if ((mask >> r) & 1u) a[r] = propensity<UM>(r, sh, L);
+        double run = a[0];
+        S[0] = run;
+#pragma unroll
+        for (int r = 1; r < RM; ++r) {
+            if (r < R) run = __dadd_rn(run, a[r]);
+            S[r] = run;
+        }
+        const double a0 = run;
+        bool done;
+        if (dbits(a0) == 0) {
+            done = true;                                   // absorbing: nothing can fire
+        } else if (draws >= budget) {
+            sh.status = PF_ST_BUDGET;
+            done = true;
+        } else {
+            const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
+                                            key1);
+            ++draws;
+            const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+            const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
+            // tau = -log(u1) / a0 with u1 = ((r0 >> 11) + 1) 2^-53 in (0, 1]
+            const double tau = __ddiv_rn(neg_log_u53((r0 >> 11) + 1ull, sh.logt), a0);
+            const double t_next = __dadd_rn(t, tau);
+            if (dbits(t_next) > t_end_bits) {
+                done = true;                               // the event lies past t_end
+            } else {
+                const uint64_t v2 = r1 >> 11;              // u2 = v2 2^-53 in [0, 1)
+                const double target = __dmul_rn(v2 ? scaled_u53(v2) : 0.0, a0);
+                const long long tb = dbits(target);
+                int chosen = 0;                            // first r with target < S_r
+#pragma unroll
+                for (int r = 0; r < RM; ++r) chosen += (r < R && dbits(S[r]) <= tb) ? 1 : 0;
+                if (chosen >= R) {                         // rounding guard
+                    chosen = 0;
+#pragma unroll
+                    for (int r = 0; r < RM; ++r)
+                        if (r < R && dbits(a[r]) != 0) chosen = r;
+                }
+                const int nch = sh.net.n_change[chosen];
+                for (int i = 0; i < nch; ++i) {
+                    const int sp = sh.net.ch_sp[chosen][i], dlt = sh.net.ch_delta[chosen][i];
+                    if constexpr (UM > 0) {
+#pragma unroll
+                        for (int u = 0; u < UM; ++u) L.x[u] += (sp == u) ? dlt : 0;
+                    } else {
+                        xs[sp * Np + L.j] += dlt;
+                    }
+                }
+                t = t_next;
+                ++fired;
+                mask = sh.net.dep[chosen];
+                done = false;
+            }
+        }
+        if (done) {
+            if constexpr (UM > 0) {
+#pragma unroll
+                for (int u = 0; u < UM; ++u)
+                    if (u < U) xs[u * Np + L.j] = L.x[u];
+            }
+            take(active);
+            t = t_prev;
+            draws = 0;
+            mask = all;
+        }
+    }
+}
+
+// Expected-work bucket of particle j for the interval (FP32, ordering only):
+// 15 - min(15, 1 + floor(log2(a0(x_j) * dt))), so heavy particles come first.
+__device__ __forceinline__ int cost_bucket(const SharedHead &sh, const int *xs, int Np, int j,
+                                           float dt) {
+    Lane<0> L;
+    L.xs = xs;
+    L.Np = Np;
+    L.j = j;
+    float a0 = 0.f;
+    for (int r = 0; r < sh.net.R; ++r)
+        a0 += sh.rate_f[r] * static_cast<float>(combos<0>(r, sh.net, L));
+    const float est = a0 * dt;
+    int b = 0;
+    if (est >= 1.f) b = min(15, ((__float_as_int(est) >> 23) & 0xFF) - 127 + 1);
+    return 15 - b;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z ^= z >> 30;
+    z *= 0xBF58476D1CE4E5B9ull;
+    z ^= z >> 27;
+    z *= 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return z;
+}
+
+// Fingerprint of slot j after the simulation step of interval k.
+__device__ __forceinline__ uint64_t slot_digest(uint32_t k, uint32_t j, uint32_t anc,
+                                                const int *xs, int Np, int U) {
+    uint64_t h = mix64((static_cast<uint64_t>(k) << 32) | j);
+    h = mix64(h ^ static_cast<uint64_t>(anc));
+    for (int u = 0; u < U; ++u) h = mix64(h ^ static_cast<uint64_t>(static_cast<uint32_t>(xs[u * Np + j])));
+    return h;
+}
+
+// Block-wide reductions (every thread receives the result).
+__device__ __forceinline__ double block_max(double v, SharedHead &sh) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.red_d[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < nw ? sh.red_d[lane] : -INFINITY;
+        for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(kFull, x, o));
+        if (lane == 0) sh.bcast_d = x;
+    }
+    __syncthreads();
+    return sh.bcast_d;
+}
+
+__device__ __forceinline__ double block_sum(double v, SharedHead &sh) {
+    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.red_d[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        double x = lane < nw ? sh.red_d[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) x = __dadd_rn(x, __shfl_xor_sync(kFull, x, o));
+        if (lane == 0) sh.bcast_d = x;
+    }
+    __syncthreads();
+    return sh.bcast_d;
+}
+
+__device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, SharedHead &sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh.red_u[warp] = v;
+    __syncthreads();
+    unsigned long long x = 0;
+    for (int i = 0; i < nw; ++i) x += sh.red_u[i];
+    return x;
+}
+
+// Inclusive prefix sum of q[0..N) in place (thread t owns a contiguous chunk).
+__device__ inline void block_scan_u64(unsigned long long *q, int N, SharedHead &sh) {
+    const int B = blockDim.x, tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31, nw = B >> 5;
+    const int chunk = (N + B - 1) / B;
+    const int beg = min(N, tid * chunk), end = min(N, beg + chunk);
+    unsigned long long run = 0;
+    for (int i = beg; i < end; ++i) {
+        run += q[i];
+        q[i] = run;
+    }
+    unsigned long long v = run;
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long n = __shfl_up_sync(kFull, v, o);
+        if (lane >= o) v += n;
+    }
+    __syncthreads();
+    if (lane == 31) sh.red_u[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long x = lane < nw ? sh.red_u[lane] : 0ull;
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long n = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += n;
+        }
+        if (lane < nw) sh.red_u[lane] = x;
+    }
+    __syncthreads();
+    const unsigned long long off = (v - run) + (warp > 0 ? sh.red_u[warp - 1] : 0ull);
+    for (int i = beg; i < end; ++i) q[i] += off;
+    __syncthreads();
+}
+
+
+// One filter -- one (theta row, observed trajectory) pair -- through all K
+// observation times (Supp. I, algorithm "Likelihood Approximation using particle
+// filter").  Called by every thread of the block.  Preconditions: sh.net and
+// sh.logt are loaded and a __syncthreads() has passed.  `arrays` holds the
+// particle population, N (16 + 8U) bytes (shared memory, or a per-block slab
+// of global memory for populations that do not fit on chip).
+struct FilterJob {
+    const double *theta;      // [d] this filter's theta row
+    const double *obs_times;  // [K]
+    const double *y;          // [K][P] this filter's trajectory
+    int K, N;
+    uint32_t mrow;            // theta index in the random-number counter
+    int traj;                 // trajectory index in the random-number counter
+    uint64_t seed, budget;
+    double *ll_out;
+    uint8_t *st_out;
+    unsigned long long *ev_out;
+    unsigned long long *dg_out;  // may be null
+    int32_t *fs_out;             // [N][U], may be null
+};
+
+template <int RM, int UM>
+__device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *arrays) {
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int d = sh.net.d, R = sh.net.R, U = sh.net.U, P = sh.net.P;
+    const int N = job.N, K = job.K;
+    const double *theta = job.theta;
+    if (tid == 0) {
+        int ok = 1;
+        for (int c = 0; c < d; ++c) {
+            const double v = theta[c];
+            if (!(isfinite(v) && v >= 0.0)) ok = 0;
+        }
+        sh.valid = ok;
+        sh.status = PF_ST_OK;
+        sh.ll = 0.0;
+        double ln = 0.0;
+        for (int p = 0; p < P; ++p) ln = __dadd_rn(ln, log(sh.net.sigma[p]));
+        sh.lognorm = __dadd_rn(ln, __dmul_rn(0.5 * static_cast<double>(P), log(2.0 * M_PI)));
+    }
+    if (tid < R) {
+        sh.rate[tid] = theta[sh.net.rate_col[tid]];
+        sh.rate_f[tid] = static_cast<float>(theta[sh.net.rate_col[tid]]);
+    }
+    __syncthreads();
+    if (!sh.valid) {
+        if (tid == 0) {
+            *job.ll_out = __longlong_as_double(0x7FF8000000000000ll);
+            *job.st_out = PF_ST_INVALID_THETA;
+            *job.ev_out = 0;
+            if (job.dg_out) *job.dg_out = 0;
+        }
+        __syncthreads();
+        return;
+    }
+
+    const int Np = N;
+    double *wbuf = reinterpret_cast<double *>(arrays);                  // [N] weights / q / Q
+    unsigned long long *qbuf = reinterpret_cast<unsigned long long *>(arrays);
+    int *xs = reinterpret_cast<int *>(wbuf + N);                       // [U][N]
+    int *xn = xs + U * Np;                                             // [U][N]
+    int *anc = xn + U * Np;                                            // [N]
+    int *order = anc + N;                                              // [N] pool order
+
+    for (int j = tid; j < N; j += B)
+        for (int u = 0; u < U; ++u) xs[u * Np + j] = sh.net.x0[u];
+    __syncthreads();
+
+    const uint32_t key0 = static_cast<uint32_t>(job.seed);
+    const uint32_t key1 = static_cast<uint32_t>(job.seed >> 32);
+    const uint32_t m32 = job.mrow;
+    const int traj = job.traj;
+    unsigned long long fired = 0, dig = 0;
+    double t_prev = 0.0;
+
+    for (int k = 0; k < K; ++k) {
+        const uint32_t lane = (static_cast<uint32_t>(traj) << 20) | static_cast<uint32_t>(k);
+        if (k > 0) {
+            // systematic resampling on the integer weights of interval k-1
+            block_scan_u64(qbuf, N, sh);
+            if (tid == 0) {
+                const unsigned long long W = qbuf[N - 1];
+                const Philox4 w = philox4x32_10(0u, kResampleLane, lane, m32, key0, key1);
+                const unsigned long long r64 = (static_cast<unsigned long long>(w.w1) << 32) | w.w0;
+                sh.u_off = __umul64hi(r64, W);
+            }
+            __syncthreads();
+            const unsigned long long W = qbuf[N - 1], u_off = sh.u_off;
+            const unsigned long long Nl = static_cast<unsigned long long>(N);
+            for (int j = tid; j < N; j += B) {
+                const unsigned long long point = u_off + static_cast<unsigned long long>(j) * W;
+                int lo = 0, hi = N - 1;  // a_j = min{i : N Q_i > point}
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (Nl * qbuf[mid] > point) hi = mid; else lo = mid + 1;
+                }
+                anc[j] = lo;
+                for (int u = 0; u < U; ++u) xn[u * Np + j] = xs[u * Np + lo];
+            }
+            __syncthreads();
+            int *tmp = xs; xs = xn; xn = tmp;
+        } else {
+            for (int j = tid; j < N; j += B) anc[j] = j;
+        }
+
+        const double t_k = job.obs_times[k];
+        if (t_k > t_prev) {
+            // pool order: counting sort of the particles by expected work, heaviest first
+            const float dt = static_cast<float>(t_k - t_prev);
+            if (tid < 16) sh.bucket[tid] = 0;
+            __syncthreads();
+            for (int j = tid; j < N; j += B) atomicAdd(&sh.bucket[cost_bucket(sh, xs, Np, j, dt)], 1);
+            __syncthreads();
+            if (tid == 0) {
+                int run = 0;
+                for (int b = 0; b < 16; ++b) {
+                    const int c = sh.bucket[b];
+                    sh.bucket[b] = run;
+                    run += c;
+                }
+                sh.pool_next = 0;
+            }
+            __syncthreads();
+            for (int j = tid; j < N; j += B)
+                order[atomicAdd(&sh.bucket[cost_bucket(sh, xs, Np, j, dt)], 1)] = j;
+            __syncthreads();
+            ssa_interval<RM, UM>(sh, xs, order, Np, N, t_prev, t_k, key0, key1, lane, m32,
+                                 job.budget, fired);
+        }
+        __syncthreads();
+        if (sh.status != PF_ST_OK) break;
+
+        if (job.dg_out)
+            for (int j = tid; j < N; j += B)
+                dig += slot_digest(static_cast<uint32_t>(k), static_cast<uint32_t>(j),
+                                   static_cast<uint32_t>(anc[j]), xs, Np, U);
+
+        // Gaussian log-weight exponent e_j = -1/2 sum_p ((y_p - (C x_j)_p) / sigma_p)^2
+        const double *yk = job.y + static_cast<int64_t>(k) * P;
+        double lmax = -INFINITY;
+        for (int j = tid; j < N; j += B) {
+            double acc = 0.0;
+            for (int p = 0; p < P; ++p) {
+                double mu = 0.0;
+                for (int u = 0; u < U; ++u)
+                    mu = __dadd_rn(mu, __dmul_rn(sh.net.C[p][u], static_cast<double>(xs[u * Np + j])));
+                const double z = __ddiv_rn(__dsub_rn(yk[p], mu), sh.net.sigma[p]);
+                acc = __dadd_rn(acc, __dmul_rn(z, z));
+            }
+            const double e = __dmul_rn(-0.5, acc);
+            wbuf[j] = e;
+            lmax = fmax(lmax, e);
+        }
+        const double emax = block_max(lmax, sh);
+        if (!isfinite(emax)) {
+            if (tid == 0) sh.status = PF_ST_NONFINITE;
+            break;
+        }
+        // p(y_k | y_<k) ~ (1/N) sum_j l_j  (Eq. likelihood approx.), in logs;
+        // the same exp() values give the integer weights for the next resampling.
+        double lsum = 0.0;
+        for (int j = tid; j < N; j += B) {
+            const double v = exp(__dsub_rn(wbuf[j], emax));
+            lsum = __dadd_rn(lsum, v);
+            qbuf[j] = __double2ull_rz(__dmul_rn(v, 4294967296.0));
+        }
+        const double s = block_sum(lsum, sh);
+        if (tid == 0) {
+            double inc = __dadd_rn(emax, log(s));
+            inc = __dsub_rn(inc, log(static_cast<double>(N)));
+            inc = __dsub_rn(inc, sh.lognorm);
+            sh.ll = __dadd_rn(sh.ll, inc);
+        }
+        t_prev = t_k;
+    }
+    __syncthreads();
+    const unsigned long long fired_all = block_sum_u64(fired, sh);
+    const unsigned long long dig_all = job.dg_out ? block_sum_u64(dig, sh) : 0ull;
+    const int status = sh.status;
+    if (tid == 0) {
+        *job.ll_out = status == PF_ST_OK ? sh.ll : -INFINITY;
+        *job.st_out = static_cast<uint8_t>(status);
+        *job.ev_out = fired_all;
+        if (job.dg_out) *job.dg_out = dig_all;
+    }
+    if (job.fs_out && status == PF_ST_OK) {
+        for (int j = tid; j < N; j += B)
+            for (int u = 0; u < U; ++u) job.fs_out[static_cast<int64_t>(j) * U + u] = xs[u * Np + j];
+    }
+    __syncthreads();
+}
+
+}  // namespace dev
+}  // namespace pf

@@ -63,6 +63,16 @@ int launch_filter(const FilterArgs &a, int block_threads, double *loglik, uint8_
 int launch_schedule(const FilterArgs &a, uint32_t *cost, uint32_t *order, uint32_t cap,
                     void *stream);
 
+// Host-side validation helpers (pf_api.cu).  fail() records a message for
+// pf_last_error() and returns `code`.
+int fail(int code, const char *fmt, ...);
+int cuda_fail(int cuda_error, const char *what);
+void clear_error();
+int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P, const double *C,
+                 const double *sigma, NetTables &t);
+int check_count_range(const NetTables &t, int K, uint64_t budget);
+int check_obs_times(const double *obs_times, int K);
+
 int launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
                   void *stream);
 

@@ -27,7 +27,9 @@ PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA = 0, 1, 2, 3
 PF_SCHED_AUTO, PF_SCHED_NATURAL, PF_SCHED_HEAVY_FIRST = 0, 1, 2
 
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
-            "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc"]
+            "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",
+            "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit", "pf_poll", "pf_ctx_stats",
+            "pf_ctx_destroy"]
 
 
 class PfError(RuntimeError):
@@ -40,6 +42,14 @@ class pf_network(ct.Structure):
     _fields_ = [("n_species", ct.c_int32), ("n_reactions", ct.c_int32),
                 ("reactants", ct.c_void_p), ("products", ct.c_void_p),
                 ("rate_index", ct.c_void_p)]
+
+
+class pf_request(ct.Structure):
+    _fields_ = [("problem_id", ct.c_int32), ("d", ct.c_int32), ("thetas", ct.c_void_p),
+                ("M", ct.c_int64), ("n_particles", ct.c_int32), ("K_use", ct.c_int32),
+                ("seed", ct.c_uint64), ("event_budget", ct.c_uint64),
+                ("loglik_threshold", ct.c_double), ("loglik", ct.c_void_p),
+                ("status", ct.c_void_p)]
 
 
 class pf_options(ct.Structure):
@@ -85,6 +95,21 @@ def load():
                                               P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P,
                                               ct.c_int32, ct.c_uint64, P, P, ct.c_uint64, P]
             lib.pf_loglik_noalloc.restype = ct.c_int
+            V = ct.c_void_p
+            lib.pf_ctx_create.argtypes = [ct.POINTER(V), ct.c_size_t, ct.c_int32, ct.c_int32]
+            lib.pf_ctx_load_problem.argtypes = [V, ct.POINTER(pf_network), ct.c_int32, P, P,
+                                                ct.c_int32, P, ct.c_int32, ct.c_int32, P, P,
+                                                ct.POINTER(ct.c_int32)]
+            lib.pf_ctx_run_batch.argtypes = [V, ct.POINTER(pf_request), ct.c_int32]
+            lib.pf_submit.argtypes = [V, ct.POINTER(pf_request), ct.POINTER(ct.c_int64)]
+            lib.pf_poll.argtypes = [V, ct.c_int64, ct.c_int32, ct.POINTER(ct.c_double),
+                                    ct.POINTER(ct.c_double)]
+            lib.pf_ctx_stats.argtypes = [V, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),
+                                         ct.POINTER(ct.c_int64)]
+            lib.pf_ctx_destroy.argtypes = [V]
+            for name in ("pf_ctx_create", "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit",
+                         "pf_poll", "pf_ctx_stats", "pf_ctx_destroy"):
+                getattr(lib, name).restype = ct.c_int
             _lib = lib
     return _lib
 
@@ -260,3 +285,87 @@ def pf_loglik_noalloc(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles
                                loglik.data_ptr(), None if status is None else status.data_ptr(),
                                ct.c_uint64(int(event_budget)), stream)
     _check(rc, "pf_loglik_noalloc")
+
+
+# --------------------------------------------------------------------------
+# batching / serving context (pf_ctx_* in include/pf1606.h)
+# --------------------------------------------------------------------------
+def pf_ctx_create(mem_budget_bytes: int = 0, n_slots: int = 0, max_particles: int = 0):
+    """Create a batching/serving context on the current device; returns a handle."""
+    lib = load()
+    h = ct.c_void_p()
+    _check(lib.pf_ctx_create(ct.byref(h), int(mem_budget_bytes), int(n_slots),
+                             int(max_particles)), "pf_ctx_create")
+    return h
+
+
+def pf_ctx_load_problem(ctx, net: dict, d: int, x0, obs_times, y, C, sigma) -> int:
+    lib = load()
+    n = _Net(net)
+    U = n.s.n_species
+    yy = _host(y, np.float64)
+    T, K, P = yy.shape
+    pid = ct.c_int32()
+    _check(lib.pf_ctx_load_problem(ctx, ct.byref(n.s), int(d), _hptr(_host(x0, np.int32)),
+                                   _hptr(_host(obs_times, np.float64)), K, _hptr(yy), T, P,
+                                   _hptr(_host(C, np.float64).reshape(P, U)),
+                                   _hptr(_host(sigma, np.float64).reshape(P)), ct.byref(pid)),
+           "pf_ctx_load_problem")
+    return pid.value
+
+
+class Request:
+    """Host arrays of one request, kept alive until pf_poll reports completion."""
+
+    def __init__(self, problem_id: int, thetas, n_particles: int, seed: int, K_use: int = 0,
+                 event_budget: int = 0, loglik_threshold: float = float("nan")):
+        self.thetas = _host(thetas, np.float64)
+        if self.thetas.ndim == 1:
+            self.thetas = self.thetas[None, :]
+        M, d = self.thetas.shape
+        self.loglik = np.full(M, np.nan)
+        self.status = np.full(M, 255, np.uint8)
+        self.s = pf_request(int(problem_id), int(d), _hptr(self.thetas), int(M),
+                            int(n_particles), int(K_use), int(seed) & (2**64 - 1),
+                            int(event_budget), float(loglik_threshold),
+                            _hptr(self.loglik), _hptr(self.status))
+        self.id = None
+        self.t_submit = self.t_done = None
+
+
+def pf_ctx_run_batch(ctx, requests) -> None:
+    """Evaluate the requests together (one batch) and wait."""
+    lib = load()
+    arr = (pf_request * len(requests))(*[r.s for r in requests])
+    _check(lib.pf_ctx_run_batch(ctx, arr, len(requests)), "pf_ctx_run_batch")
+
+
+def pf_submit(ctx, request: Request) -> int:
+    lib = load()
+    rid = ct.c_int64()
+    _check(lib.pf_submit(ctx, ct.byref(request.s), ct.byref(rid)), "pf_submit")
+    request.id = rid.value
+    return rid.value
+
+
+def pf_poll(ctx, request: Request, wait_ms: int = 0) -> bool:
+    """True when finished (results are in request.loglik / request.status)."""
+    lib = load()
+    ts, td = ct.c_double(), ct.c_double()
+    rc = lib.pf_poll(ctx, int(request.id), int(wait_ms), ct.byref(ts), ct.byref(td))
+    if rc == PF_EAGAIN:
+        return False
+    _check(rc, "pf_poll")
+    request.t_submit, request.t_done = ts.value, td.value
+    return True
+
+
+def pf_ctx_stats(ctx):
+    lib = load()
+    b, r, f = ct.c_int64(), ct.c_int64(), ct.c_int64()
+    _check(lib.pf_ctx_stats(ctx, ct.byref(b), ct.byref(r), ct.byref(f)), "pf_ctx_stats")
+    return {"batches": b.value, "requests": r.value, "filters": f.value}
+
+
+def pf_ctx_destroy(ctx) -> None:
+    _check(load().pf_ctx_destroy(ctx), "pf_ctx_destroy")

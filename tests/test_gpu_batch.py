@@ -1,0 +1,145 @@
+"""Batching and serving through the C ABI context (pf_ctx_*).
+
+A request's result depends only on its own inputs, so every request in a
+batch -- whatever else shares the launch -- must equal the plain pf_loglik
+call with the same problem, theta, N, observation prefix and seed, bit for
+bit.  Requests mix problems, theta counts, particle counts (shared-memory and
+global-memory populations) and observation prefixes.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+from paper_1606_08281_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_08281_gb300 import build, pf as pfmod
+    build.build()
+    pfmod.load()
+    return pfmod
+
+
+@pytest.fixture(scope="module")
+def ctx(pf):
+    c = pf.pf_ctx_create(mem_budget_bytes=0, n_slots=3, max_particles=4096)
+    yield c
+    pf.pf_ctx_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def problems(pf, ctx):
+    out = {}
+    for name in ("birth_death", "gene_expression", "cascade"):
+        w = W.get(name)
+        d = w.R
+        pid = pf.pf_ctx_load_problem(ctx, w.net, d, w.x0, w.obs_times, w.observations(), w.C,
+                                     w.sigma)
+        out[name] = (pid, w)
+    return out
+
+
+def plain(pf, w, th, N, seed, K):
+    return pf.pf_loglik(w.net, th, w.x0, w.obs_times[:K], w.observations()[:, :K, :], w.C,
+                        w.sigma, N, seed)
+
+
+SPECS = [  # (problem, M, N, K, seed)
+    ("birth_death", 37, 100, 20, 11),
+    ("gene_expression", 9, 1000, 12, 12),        # population on chip
+    ("gene_expression", 3, 2048, 6, 13),         # population in the global slab
+    ("cascade", 2, 256, 4, 14),
+    ("cascade", 1, 600, 3, 15),                  # cascade in the global slab
+    ("birth_death", 1, 1, 5, 16),                # a single particle
+    ("gene_expression", 0, 64, 5, 17),           # an empty request
+]
+
+
+def make_requests(pf, problems, specs):
+    reqs = []
+    for name, M, N, K, seed in specs:
+        pid, w = problems[name]
+        th = W.log_uniform(np.random.default_rng(seed), w.prior_lo, w.prior_hi, max(M, 0))
+        reqs.append((pf.Request(pid, th, N, seed, K_use=K), w, th, N, seed, K))
+    return reqs
+
+
+def test_batch_matches_plain_calls(pf, ctx, problems):
+    reqs = make_requests(pf, problems, SPECS)
+    pf.pf_ctx_run_batch(ctx, [r[0] for r in reqs])
+    for r, w, th, N, seed, K in reqs:
+        ref = plain(pf, w, th, N, seed, K)
+        assert (r.status == ref["status"]).all()
+        assert np.array_equal(r.loglik, ref["loglik"]), (w.name, N, K)
+
+
+def test_result_alone_equals_result_in_the_mix(pf, ctx, problems):
+    reqs = make_requests(pf, problems, SPECS)
+    target = reqs[1]
+    alone = make_requests(pf, problems, [SPECS[1]])[0]
+    pf.pf_ctx_run_batch(ctx, [alone[0]])
+    pf.pf_ctx_run_batch(ctx, [r[0] for r in reqs])
+    assert np.array_equal(alone[0].loglik, target[0].loglik)
+
+
+def test_serving_submit_and_poll(pf, ctx, problems):
+    specs = [SPECS[i % 5] for i in range(12)]
+    specs = [(n, M, N, K, 100 + i) for i, (n, M, N, K, _) in enumerate(specs)]
+    reqs = make_requests(pf, problems, specs)
+    for r in reqs:
+        pf.pf_submit(ctx, r[0])
+    for r, w, th, N, seed, K in reqs:
+        while not pf.pf_poll(ctx, r, wait_ms=1000):
+            pass
+        ref = plain(pf, w, th, N, seed, K)
+        assert np.array_equal(r.loglik, ref["loglik"])
+        assert r.t_done >= r.t_submit
+    st = pf.pf_ctx_stats(ctx)
+    assert st["requests"] >= len(reqs) and st["batches"] >= 1
+
+
+def test_admission_by_memory_budget(pf, problems):
+    """A small budget admits requests a few at a time; all still finish with the
+    right results, and a request larger than the budget is refused."""
+    small = pf.pf_ctx_create(mem_budget_bytes=40_000, n_slots=2, max_particles=1024)
+    try:
+        pids = {}
+        for name in ("birth_death", "gene_expression"):
+            w = W.get(name)
+            pids[name] = pf.pf_ctx_load_problem(small, w.net, w.R, w.x0, w.obs_times,
+                                                w.observations(), w.C, w.sigma)
+        probs = {k: (pids[k], W.get(k)) for k in pids}
+        specs = [("birth_death", 40, 100, 20, 200 + i) for i in range(6)]
+        specs += [("gene_expression", 8, 200, 5, 300 + i) for i in range(3)]
+        reqs = make_requests(pf, probs, specs)
+        for r in reqs:
+            pf.pf_submit(small, r[0])
+        for r, w, th, N, seed, K in reqs:
+            while not pf.pf_poll(small, r, wait_ms=1000):
+                pass
+            assert np.array_equal(r.loglik, plain(pf, w, th, N, seed, K)["loglik"])
+        assert pf.pf_ctx_stats(small)["batches"] >= 3
+        big = make_requests(pf, probs, [("gene_expression", 4000, 64, 5, 1)])[0][0]
+        with pytest.raises(pf.PfError) as e:
+            pf.pf_submit(small, big)
+        assert e.value.code == pf.PF_EBUSY
+    finally:
+        pf.pf_ctx_destroy(small)
+
+
+def test_bad_requests(pf, ctx, problems):
+    pid, w = problems["birth_death"]
+    with pytest.raises(pf.PfError) as e:
+        pf.pf_submit(ctx, pf.Request(99, np.ones((1, 2)), 10, 1))
+    assert e.value.code == pf.PF_ENOTFOUND
+    with pytest.raises(pf.PfError):
+        pf.pf_submit(ctx, pf.Request(pid, np.ones((1, 2)), 10, 1, K_use=999))
+    with pytest.raises(pf.PfError):
+        pf.pf_submit(ctx, pf.Request(pid, np.ones((1, 2)), 100000, 1))
