@@ -221,6 +221,11 @@ def main() -> None:
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--probe-only", action="store_true",
                     help="run the FP64 cost probe alone and print it")
+    ap.add_argument("--mode", default="step", choices=["step", "hetero", "serve"],
+                    help="step: the contract's timed step; hetero: one batch of a "
+                         "heterogeneous request mix vs plain per-request launches; serve: a "
+                         "Poisson request stream, continuous batching vs a plain FIFO server")
+    ap.add_argument("--serve-seconds", type=float, default=10.0)
     a = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -243,6 +248,9 @@ def main() -> None:
     pf.load()
     if a.probe_only:
         print(json.dumps(fp64_probe(pf)), flush=True)
+        return
+    if a.mode != "step":
+        run_pattern(a)
         return
 
     w = W.get(a.workload)
@@ -362,6 +370,32 @@ def main() -> None:
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def run_pattern(a) -> None:
+    """Batching / serving measurements (one JSON line each)."""
+    from paper_1606_08281_gb300 import serving
+    if a.mode == "hetero":
+        mix = W.hetero_mix()
+        res = serving.run_hetero(mix, repeats=2)
+        line = {"metric": "theta-likelihoods/s", "mode": "hetero-batch",
+                "value": res["batched_theta_per_s"], "unit": "theta-likelihoods/s",
+                "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "heterogeneous mix: 48 requests over birth_death / "
+                                       "gene_expression / cascade, theta 1-4096 (cascade 1-64), "
+                                       "N 256-4096, K 10-100 (seed 4001)"},
+                "plain_per_request": res["plain_theta_per_s"], **res}
+    else:
+        stream = W.serving_stream(duration_s=a.serve_seconds)
+        res = serving.run_serving(stream)
+        line = {"metric": "theta-likelihoods/s", "mode": "serving",
+                "value": res["batched"]["theta_per_s"], "unit": "theta-likelihoods/s",
+                "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"Poisson 200/s for {a.serve_seconds:.0f} s (seed 5001): "
+                                       "gene_expression (theta 4-512, N 256, K 10) and cascade "
+                                       "(theta 1-32, N 128, K 5), coin-flipped"},
+                **res}
+    print(json.dumps(line), flush=True)
 
 
 def fp64_probe(pf) -> dict:

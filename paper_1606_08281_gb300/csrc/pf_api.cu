@@ -196,11 +196,12 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     if (B == 0) B = std::min(128, ((N + 31) / 32) * 32);
     if (B < 32 || B > 256 || (B % 32)) return fail(PF_EINVAL, "block_threads %d must be a multiple of 32 in 32..256", B);
     const size_t smem = pf::filter_smem_bytes(N, a.net.U, B);
-    int dev = 0, smem_max = 0;
+    int dev = 0, smem_max = 0, sms = 0;
     PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     PF_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
-    if (smem + sizeof(pf::NetTables) + 2048 > (size_t)smem_max)
-        return fail(PF_EINVAL, "N=%d with U=%d needs %zu bytes of shared memory per filter (limit %d)", N, a.net.U, smem, smem_max);
+    PF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    // populations that do not fit on chip (with the block's static tables) go to global memory
+    const bool on_chip = smem + 16384 <= (size_t)smem_max;
 
     cudaStream_t s = static_cast<cudaStream_t>(o.stream);
     // observation times (always a host array): strictly increasing, >= 0, finite
@@ -271,7 +272,13 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
         if (e) return cuda_fail((cudaError_t)e, "schedule launch");
         a.row_order = (const uint32_t *)b_order.p;
     }
-    int e = pf::launch_filter(a, B, d_ll, d_st, s);
+    DevBuf b_slab;
+    int grid = 0;
+    if (!on_chip) {
+        grid = (int)std::min<int64_t>(F, pf::global_grid(sms));
+        PF_CUDA(b_slab.alloc(smem * (size_t)grid, s), "alloc global populations");
+    }
+    int e = pf::launch_filter(a, B, d_ll, d_st, s, (unsigned char *)b_slab.p, smem, grid);
     if (e) return cuda_fail((cudaError_t)e, "filter launch");
 
     if (!o.device_ptrs) {

@@ -71,6 +71,58 @@ __global__ void __launch_bounds__(256, 2) filter_kernel(const FilterArgs args) {
     run_filter<RM, UM>(job, sh, smem);
 }
 
+// Populations too large for shared memory: a grid of resident blocks walks
+// the filters (grid stride), each block keeping its population in its own slab
+// of global memory (N (16 + 8U) bytes), which stays in L1/L2 while it runs.
+template <int RM, int UM>
+__global__ void __launch_bounds__(256, 2) filter_kernel_global(const FilterArgs args,
+                                                               unsigned char *slabs,
+                                                               size_t slab_bytes) {
+    __shared__ SharedHead sh;
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int T = args.T;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&args.net);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sh.net);
+        for (int i = tid; i < static_cast<int>(sizeof(NetTables) / 4); i += B) dst[i] = src[i];
+    }
+    load_log_table(sh.logt);
+    unsigned char *arrays = slabs + static_cast<size_t>(blockIdx.x) * slab_bytes;
+    const int64_t F = args.M * T;
+    for (int64_t slot = blockIdx.x; slot < F; slot += gridDim.x) {
+        __syncthreads();
+        int64_t mrow = slot / T;
+        const int traj = static_cast<int>(slot - mrow * T);
+        if (args.row_order) mrow = args.row_order[mrow];
+        const int64_t f = mrow * T + traj;
+        FilterJob job;
+        job.theta = args.thetas + mrow * args.net.d;
+        job.obs_times = args.obs_times;
+        job.y = args.y + static_cast<int64_t>(traj) * args.K * args.net.P;
+        job.K = args.K;
+        job.N = args.N;
+        job.mrow = static_cast<uint32_t>(mrow);
+        job.traj = traj;
+        job.seed = args.seed;
+        job.budget = args.budget;
+        job.ll_out = args.ll_f + f;
+        job.st_out = args.st_f + f;
+        job.ev_out = reinterpret_cast<unsigned long long *>(args.ev_f) + f;
+        job.dg_out = args.dg_f ? reinterpret_cast<unsigned long long *>(args.dg_f) + f : nullptr;
+        job.fs_out = args.final_states
+                         ? args.final_states + f * static_cast<int64_t>(args.N) * args.net.U
+                         : nullptr;
+        run_filter<RM, UM>(job, sh, arrays);
+    }
+}
+
+template <int RM, int UM>
+int launch_tier_global(const FilterArgs &a, int B, unsigned char *slabs, size_t slab_bytes,
+                       int grid, cudaStream_t s) {
+    filter_kernel_global<RM, UM><<<grid, B, 0, s>>>(a, slabs, slab_bytes);
+    return cudaGetLastError();
+}
+
 // loglik[m] = sum over trajectories (in order) of the filter estimates (Supp. I).
 __global__ void reduce_kernel(const double *ll_f, const uint8_t *st_f, int64_t M, int T,
                               double *loglik, uint8_t *status) {
@@ -225,13 +277,25 @@ int reaction_tier(int R) {
     return 32;
 }
 
-int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, void *stream) {
+int global_grid(int sms) { return sms * 2; }
+
+int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, void *stream,
+                  unsigned char *slabs, size_t slab_bytes, int grid) {
     if (a.M == 0) return cudaSuccess;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t smem = filter_smem_bytes(a.N, a.net.U, B);
     int e;
     const bool small_u = a.net.U <= 4;
-    switch (reaction_tier(a.net.R)) {
+    if (slabs) {
+        switch (reaction_tier(a.net.R)) {
+            case 4: e = small_u ? launch_tier_global<4, 4>(a, B, slabs, slab_bytes, grid, s)
+                                : launch_tier_global<4, 0>(a, B, slabs, slab_bytes, grid, s); break;
+            case 8: e = small_u ? launch_tier_global<8, 4>(a, B, slabs, slab_bytes, grid, s)
+                                : launch_tier_global<8, 0>(a, B, slabs, slab_bytes, grid, s); break;
+            case 16: e = launch_tier_global<16, 0>(a, B, slabs, slab_bytes, grid, s); break;
+            default: e = launch_tier_global<32, 0>(a, B, slabs, slab_bytes, grid, s); break;
+        }
+    } else switch (reaction_tier(a.net.R)) {
         case 4: e = small_u ? launch_tier<4, 4>(a, B, smem, s) : launch_tier<4, 0>(a, B, smem, s); break;
         case 8: e = small_u ? launch_tier<8, 4>(a, B, smem, s) : launch_tier<8, 0>(a, B, smem, s); break;
         case 16: e = launch_tier<16, 0>(a, B, smem, s); break;

@@ -50,10 +50,16 @@ size_t filter_smem_bytes(int N, int U, int block_threads);
 // Largest reaction-count template that fits R.
 int reaction_tier(int R);
 
-// Launch the filter kernel and the per-theta reduction on `stream`.
+// Launch the filter kernel and the per-theta reduction on `stream`.  With
+// `slabs` non-null the populations live in global memory: `grid` resident
+// blocks walk the filters, block b using slabs + b * slab_bytes.
 // Returns a cudaError_t value (0 on success).
 int launch_filter(const FilterArgs &a, int block_threads, double *loglik, uint8_t *status,
-                  void *stream);
+                  void *stream, unsigned char *slabs = nullptr, size_t slab_bytes = 0,
+                  int grid = 0);
+
+// Resident blocks for the global-memory variant on a GPU with `sms` SMs.
+int global_grid(int sms);
 
 // Heaviest-first launch order of the theta rows: a pilot kernel simulates
 // one unconditioned path per row over [0, t_K] (its own random stream, at most

@@ -1,0 +1,146 @@
+"""Drivers for the batching and serving patterns (measurement and examples).
+
+run_hetero:  a heterogeneous set of requests evaluated (a) as one batch of the
+             context (persistent kernels, one graph replay) and (b) as plain
+             per-request pf_loglik launches, one after another.
+run_serving: a Poisson stream of level-set batches served (a) by the context's
+             continuous-batching worker (submit at arrival, several batches in
+             flight) and (b) by a plain FIFO server that runs each request with
+             its own pf_loglik launch.
+Both check that the two arms give bit-identical log-likelihoods, and report
+theta-likelihoods/s and latency percentiles.
+"""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+
+from . import pf
+from . import workloads as W
+
+
+def _load_problems(ctx, names):
+    ids = {}
+    for name in names:
+        w = W.get(name)
+        ids[name] = pf.pf_ctx_load_problem(ctx, w.net, w.R, w.x0, w.obs_times, w.observations(),
+                                           w.C, w.sigma)
+    return ids
+
+
+def _plain(spec, w):
+    K = spec.K_use
+    return pf.pf_loglik(w.net, spec.thetas, w.x0, w.obs_times[:K], w.observations()[:, :K, :],
+                        w.C, w.sigma, spec.n_particles, spec.seed)
+
+
+def run_hetero(mix, n_slots: int = 3, repeats: int = 1) -> dict:
+    names = sorted({s.problem for s in mix})
+    wl = {n: W.get(n) for n in names}
+    rows = sum(len(s.thetas) for s in mix)
+    ctx = pf.pf_ctx_create(0, n_slots, 4096)
+    try:
+        ids = _load_problems(ctx, names)
+        # warm-up: one small request per problem
+        pf.pf_ctx_run_batch(ctx, [pf.Request(ids[n], wl[n].thetas(1), 64, 1, K_use=2)
+                                  for n in names])
+        batched = []
+        for _ in range(repeats):
+            reqs = [pf.Request(ids[s.problem], s.thetas, s.n_particles, s.seed, K_use=s.K_use)
+                    for s in mix]
+            t0 = time.perf_counter()
+            pf.pf_ctx_run_batch(ctx, reqs)
+            batched.append(time.perf_counter() - t0)
+        stats = pf.pf_ctx_stats(ctx)
+    finally:
+        pf.pf_ctx_destroy(ctx)
+    _plain(mix[0], wl[mix[0].problem])  # warm-up
+    t0 = time.perf_counter()
+    plain = [_plain(s, wl[s.problem]) for s in mix]
+    t_plain = time.perf_counter() - t0
+    same = all(np.array_equal(r.loglik, p["loglik"]) for r, p in zip(reqs, plain))
+    tb = float(np.min(batched))
+    return {"requests": len(mix), "theta_rows": rows,
+            "batched_s": tb, "plain_s": t_plain,
+            "batched_theta_per_s": rows / tb, "plain_theta_per_s": rows / t_plain,
+            "speedup": t_plain / tb, "identical_results": bool(same),
+            "filters": int(stats["filters"] // (repeats + 1) if repeats else 0)}
+
+
+def _percentiles(lat):
+    lat = np.asarray(lat)
+    return {"p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "mean_ms": 1e3 * float(lat.mean()), "max_ms": 1e3 * float(lat.max())}
+
+
+def serve_batched(stream, n_slots: int = 3, mem_budget: int = 0) -> dict:
+    names = sorted({s.problem for s in stream})
+    wl = {n: W.get(n) for n in names}
+    ctx = pf.pf_ctx_create(mem_budget, n_slots, 4096)
+    try:
+        ids = _load_problems(ctx, names)
+        pf.pf_ctx_run_batch(ctx, [pf.Request(ids[n], wl[n].thetas(1), 64, 1, K_use=2)
+                                  for n in names])
+        reqs = [pf.Request(ids[s.problem], s.thetas, s.n_particles, s.seed, K_use=s.K_use,
+                           loglik_threshold=s.threshold) for s in stream]
+        submit_clock = {}
+        done = threading.Event()
+
+        def submitter():
+            t0 = time.perf_counter()
+            for r, s in zip(reqs, stream):
+                dt = s.arrival_s - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                pf.pf_submit(ctx, r)
+                submit_clock[r.id] = time.perf_counter()
+            done.set()
+
+        th = threading.Thread(target=submitter)
+        th.start()
+        lat = []
+        finish = []
+        for r in reqs:
+            while r.id is None:
+                time.sleep(0.0005)
+            while not pf.pf_poll(ctx, r, wait_ms=50):
+                pass
+            lat.append(r.t_done - r.t_submit)
+            finish.append(r.t_done)
+        th.join()
+        span = max(finish) - min(r.t_submit for r in reqs)
+        stats = pf.pf_ctx_stats(ctx)
+    finally:
+        pf.pf_ctx_destroy(ctx)
+    rows = sum(len(s.thetas) for s in stream)
+    return {"theta_per_s": rows / span, "span_s": span, "batches": stats["batches"],
+            **_percentiles(lat), "loglik": [r.loglik for r in reqs]}
+
+
+def serve_plain(stream) -> dict:
+    """FIFO server: each request runs as its own pf_loglik launch, in arrival
+    order, as soon as the previous one finished."""
+    wl = {n: W.get(n) for n in {s.problem for s in stream}}
+    _plain(stream[0], wl[stream[0].problem])  # warm-up
+    t0 = time.perf_counter()
+    lat, outs = [], []
+    for s in stream:
+        now = time.perf_counter() - t0
+        if s.arrival_s > now:
+            time.sleep(s.arrival_s - now)
+        outs.append(_plain(s, wl[s.problem])["loglik"])
+        lat.append(time.perf_counter() - t0 - s.arrival_s)
+    span = time.perf_counter() - t0 - stream[0].arrival_s
+    rows = sum(len(s.thetas) for s in stream)
+    return {"theta_per_s": rows / span, "span_s": span, **_percentiles(lat), "loglik": outs}
+
+
+def run_serving(stream, n_slots: int = 3) -> dict:
+    b = serve_batched(stream, n_slots)
+    p = serve_plain(stream)
+    same = all(np.array_equal(x, y) for x, y in zip(b.pop("loglik"), p.pop("loglik")))
+    return {"requests": len(stream), "theta_rows": int(sum(len(s.thetas) for s in stream)),
+            "batched": b, "plain": p, "identical_results": bool(same)}

@@ -228,3 +228,69 @@ def load_observations(name: str, path: Path = OBSERVATIONS_PATH) -> np.ndarray:
     with open(path) as f:
         data = json.load(f)
     return np.array(data[name]["y"], dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# request mixes for the batching and serving patterns
+# --------------------------------------------------------------------------
+@dataclass
+class RequestSpec:
+    problem: str            # workload name
+    thetas: np.ndarray      # [M][d]
+    n_particles: int
+    K_use: int
+    seed: int
+    arrival_s: float = 0.0
+    threshold: float = float("nan")
+
+
+def hetero_mix(seed: int = 4001, n_requests: int = 48, max_theta: int = 4096,
+               max_theta_cascade: int = 64) -> list[RequestSpec]:
+    """Heterogeneous batch: problems uniform over the three networks, theta
+    counts log-uniform integers in [1, max_theta] ([1, max_theta_cascade] for
+    the 10-species cascade, whose filters cost ~100x more), particle counts
+    uniform over {256, 512, 1024, 2048, 4096}, observation prefix K uniform in
+    [10, 100] capped at the problem's K."""
+    rng = np.random.default_rng(seed)
+    names = ["birth_death", "gene_expression", "cascade"]
+    wl = {n: get(n) for n in names}
+    out = []
+    for i in range(n_requests):
+        name = names[int(rng.integers(3))]
+        w = wl[name]
+        hi = max_theta_cascade if name == "cascade" else max_theta
+        M = int(np.floor(np.exp(rng.uniform(0.0, np.log(hi + 1)))))
+        M = max(1, min(hi, M))
+        N = int(rng.choice([256, 512, 1024, 2048, 4096]))
+        K = min(w.K, int(rng.integers(10, 101)))
+        th = log_uniform(rng, w.prior_lo, w.prior_hi, M)
+        out.append(RequestSpec(name, th, N, K, int(seed * 1000 + i)))
+    return out
+
+
+def serving_stream(seed: int = 5001, rate_hz: float = 200.0, duration_s: float = 10.0,
+                   theta_range=(4, 512), cascade_theta_range=(1, 32)) -> list[RequestSpec]:
+    """Poisson arrivals of level-set batches: a seeded coin picks the
+    gene-expression or the cascade network; theta counts are log-uniform in
+    the given ranges; N = 256 (gene expression, first 10 observation times) or
+    128 (cascade, first 5).  Each request carries the median log-likelihood of
+    the previous request of its network as its level-set threshold (the
+    alpha = 50% quantile rule of the sampler), informational only."""
+    rng = np.random.default_rng(seed)
+    wl = {n: get(n) for n in ("gene_expression", "cascade")}
+    t = 0.0
+    out = []
+    i = 0
+    while True:
+        t += rng.exponential(1.0 / rate_hz)
+        if t > duration_s:
+            break
+        name = "gene_expression" if rng.random() < 0.5 else "cascade"
+        w = wl[name]
+        lo, hi = theta_range if name == "gene_expression" else cascade_theta_range
+        M = int(np.clip(np.floor(np.exp(rng.uniform(np.log(lo), np.log(hi + 1)))), lo, hi))
+        N, K = (256, 10) if name == "gene_expression" else (128, 5)
+        th = log_uniform(rng, w.prior_lo, w.prior_hi, M)
+        out.append(RequestSpec(name, th, N, K, int(seed * 100000 + i), arrival_s=t))
+        i += 1
+    return out

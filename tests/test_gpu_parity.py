@@ -105,6 +105,20 @@ def test_particle_counts_and_block_sizes(pf, N, B):
     assert_parity(g, o)
 
 
+def test_global_memory_populations(pf):
+    """Populations beyond shared memory run from global-memory slabs: the
+    cascade with 4096 particles (393 KB) and birth-death with the maximum
+    16384 particles."""
+    w = W.cascade().subset(T=2, K=2)
+    g, o = run_both(pf, w.net, w.thetas(2), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                    4096, 21, final_states=True)
+    assert_parity(g, o, final_states=True)
+    w = W.birth_death()
+    g, o = run_both(pf, w.net, w.thetas(3), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
+                    16384, 22)
+    assert_parity(g, o)
+
+
 def test_observation_at_time_zero_and_single_time(pf):
     w = W.birth_death()
     y = np.array([[[3.3], [7.0]]])
