@@ -95,7 +95,7 @@ typedef struct {
  *                 host arrays (small; copied by the call).
  *   stream        cudaStream_t to use (NULL = the legacy default stream).
  *   block_threads threads per filter block (0 = library choice; else a
- *                 multiple of 32 in 32..256).
+ *                 multiple of 32 in 32..128).
  *   ll_traj       optional [M][T] per-filter log-likelihood (-inf when the
  *                 filter failed).
  *   events        optional [M][T] number of reactions fired per filter.

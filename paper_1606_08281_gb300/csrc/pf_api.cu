@@ -194,7 +194,7 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     if (rc) return rc;
     int B = o.block_threads;
     if (B == 0) B = std::min(128, ((N + 31) / 32) * 32);
-    if (B < 32 || B > 256 || (B % 32)) return fail(PF_EINVAL, "block_threads %d must be a multiple of 32 in 32..256", B);
+    if (B < 32 || B > 128 || (B % 32)) return fail(PF_EINVAL, "block_threads %d must be a multiple of 32 in 32..128", B);
     const size_t smem = pf::filter_smem_bytes(N, a.net.U, B);
     int dev = 0, smem_max = 0, sms = 0;
     PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");

@@ -96,8 +96,8 @@ def test_cascade_subset(pf):
     assert_parity(g, o, final_states=True)
 
 
-@pytest.mark.parametrize("N,B", [(1, 0), (2, 0), (33, 0), (100, 32), (257, 256), (1000, 128),
-                                 (4096, 256)])
+@pytest.mark.parametrize("N,B", [(1, 0), (2, 0), (33, 0), (100, 32), (257, 64), (1000, 128),
+                                 (4096, 96)])
 def test_particle_counts_and_block_sizes(pf, N, B):
     w = W.gene_expression().subset(T=2, K=6)
     g, o = run_both(pf, w.net, w.thetas(4), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
