@@ -75,7 +75,7 @@ __global__ void reset_kernel(unsigned long long *counters) {
 }
 
 template <int RM, int UM, bool GLOBAL>
-__global__ void __launch_bounds__(kBlock, 5)
+__global__ void __launch_bounds__(kBlock, 4)
 batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *items, int group,
              unsigned long long *counters, unsigned char *slab, size_t slab_bytes, double *ll_f,
              uint8_t *st_f, unsigned long long *ev_f) {
@@ -189,8 +189,8 @@ int tier_of(const NetTables &t) {
 }
 
 // Shared-memory population arena of the on-chip groups (bytes): tier 0 is
-// sized so that five blocks fit an SM with 1000-particle, 2-species filters.
-size_t shared_arena(int tier) { return tier == 0 ? 34000u : 48u << 10; }
+// sized so that four blocks fit an SM (gene-expression sized filters).
+size_t shared_arena(int tier) { return tier == 0 ? 40u << 10 : 48u << 10; }
 
 size_t population_bytes(int N, int U) { return filter_smem_bytes(N, U, kBlock); }
 

@@ -35,7 +35,7 @@ using namespace dev;
 
 // ------------------------------------------------------------------ kernels
 template <int RM, int UM>
-__global__ void __launch_bounds__(128, 5) filter_kernel(const FilterArgs args) {
+__global__ void __launch_bounds__(128, 4) filter_kernel(const FilterArgs args) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SharedHead sh;
     const int tid = threadIdx.x, B = blockDim.x;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(128, 5) filter_kernel(const FilterArgs args) {
 // the filters (grid stride), each block keeping its population in its own slab
 // of global memory (N (16 + 8U) bytes), which stays in L1/L2 while it runs.
 template <int RM, int UM>
-__global__ void __launch_bounds__(128, 5) filter_kernel_global(const FilterArgs args,
+__global__ void __launch_bounds__(128, 4) filter_kernel_global(const FilterArgs args,
                                                                unsigned char *slabs,
                                                                size_t slab_bytes) {
     __shared__ SharedHead sh;
