@@ -195,7 +195,7 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     int B = o.block_threads;
     if (B == 0) B = std::min(128, ((N + 31) / 32) * 32);
     if (B < 32 || B > 128 || (B % 32)) return fail(PF_EINVAL, "block_threads %d must be a multiple of 32 in 32..128", B);
-    const size_t smem = pf::filter_smem_bytes(N, a.net.U, B);
+    const size_t smem = pf::filter_smem_bytes(N, a.net.U, o.digest != nullptr);
     int dev = 0, smem_max = 0, sms = 0;
     PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     PF_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
@@ -378,7 +378,7 @@ extern "C" int pf_loglik_noalloc(const pf_network *net, const double *thetas, in
     rc = check_count_range(a.net, K, budget);
     if (rc) return rc;
     const int B = std::min(128, ((N + 31) / 32) * 32);
-    const size_t smem = pf::filter_smem_bytes(N, a.net.U, B);
+    const size_t smem = pf::filter_smem_bytes(N, a.net.U, false);
     int dev = 0, smem_max = 0;
     PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     PF_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");

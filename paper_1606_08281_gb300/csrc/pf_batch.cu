@@ -192,7 +192,7 @@ int tier_of(const NetTables &t) {
 // sized so that four blocks fit an SM (gene-expression sized filters).
 size_t shared_arena(int tier) { return tier == 0 ? 40u << 10 : 48u << 10; }
 
-size_t population_bytes(int N, int U) { return filter_smem_bytes(N, U, kBlock); }
+size_t population_bytes(int N, int U) { return filter_smem_bytes(N, U, false); }
 
 double now_s(std::chrono::steady_clock::time_point t0) {
     return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -381,12 +381,17 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
     }
 
     const int Np = N;
-    double *wbuf = reinterpret_cast<double *>(arrays);                  // [N] weights / q / Q
+    const bool want_digest = job.dg_out != nullptr;
+    // population layout (filter_smem_bytes): [N] 8-byte weights / integer
+    // weights / prefix sums, also the staging area of the gather | states
+    // int32 [U][N] | [N] pool order, also the ancestors during the gather |
+    // [N] ancestors, kept only for the digest
+    double *wbuf = reinterpret_cast<double *>(arrays);
     unsigned long long *qbuf = reinterpret_cast<unsigned long long *>(arrays);
-    int *xs = reinterpret_cast<int *>(wbuf + N);                       // [U][N]
-    int *xn = xs + U * Np;                                             // [U][N]
-    int *anc = xn + U * Np;                                            // [N]
-    int *order = anc + N;                                              // [N] pool order
+    int *stage = reinterpret_cast<int *>(arrays);
+    int *xs = reinterpret_cast<int *>(wbuf + N);
+    int *order = xs + U * Np;
+    int *anc = order + N;
 
     for (int j = tid; j < N; j += B)
         for (int u = 0; u < U; ++u) xs[u * Np + j] = sh.net.x0[u];
@@ -420,12 +425,26 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
                     const int mid = (lo + hi) >> 1;
                     if (Nl * qbuf[mid] > point) hi = mid; else lo = mid + 1;
                 }
-                anc[j] = lo;
-                for (int u = 0; u < U; ++u) xn[u * Np + j] = xs[u * Np + lo];
+                order[j] = lo;
+                if (want_digest) anc[j] = lo;
             }
             __syncthreads();
-            int *tmp = xs; xs = xn; xn = tmp;
-        } else {
+            // gather x'_j = x_{a_j} through the staging area, two species per pass
+            for (int u0 = 0; u0 < U; u0 += 2) {
+                const bool two = u0 + 1 < U;
+                for (int j = tid; j < N; j += B) {
+                    const int a = order[j];
+                    stage[2 * j] = xs[u0 * Np + a];
+                    if (two) stage[2 * j + 1] = xs[(u0 + 1) * Np + a];
+                }
+                __syncthreads();
+                for (int j = tid; j < N; j += B) {
+                    xs[u0 * Np + j] = stage[2 * j];
+                    if (two) xs[(u0 + 1) * Np + j] = stage[2 * j + 1];
+                }
+                __syncthreads();
+            }
+        } else if (want_digest) {
             for (int j = tid; j < N; j += B) anc[j] = j;
         }
 
@@ -456,7 +475,7 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
         __syncthreads();
         if (sh.status != PF_ST_OK) break;
 
-        if (job.dg_out)
+        if (want_digest)
             for (int j = tid; j < N; j += B)
                 dig += slot_digest(static_cast<uint32_t>(k), static_cast<uint32_t>(j),
                                    static_cast<uint32_t>(anc[j]), xs, Np, U);

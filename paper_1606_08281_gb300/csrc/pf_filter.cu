@@ -265,9 +265,8 @@ int launch_tier(const FilterArgs &a, int B, size_t smem, cudaStream_t s) {
 
 }  // namespace
 
-size_t filter_smem_bytes(int N, int U, int /*block_threads*/) {
-    return static_cast<size_t>(N) * 8 + 2 * static_cast<size_t>(U) * N * 4 +
-           2 * static_cast<size_t>(N) * 4 + 16;
+size_t filter_smem_bytes(int N, int U, bool digest) {
+    return static_cast<size_t>(N) * (8 + 4 * static_cast<size_t>(U) + 4 + (digest ? 4 : 0)) + 16;
 }
 
 int reaction_tier(int R) {
@@ -283,7 +282,7 @@ int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, v
                   unsigned char *slabs, size_t slab_bytes, int grid) {
     if (a.M == 0) return cudaSuccess;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t smem = filter_smem_bytes(a.N, a.net.U, B);
+    const size_t smem = filter_smem_bytes(a.N, a.net.U, a.dg_f != nullptr);
     int e;
     const bool small_u = a.net.U <= 4;
     if (slabs) {

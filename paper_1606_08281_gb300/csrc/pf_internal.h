@@ -44,8 +44,9 @@ struct FilterArgs {
     const uint32_t *row_order;  // [M] theta rows in launch order (null: 0..M-1)
 };
 
-// Bytes of dynamic shared memory the filter kernel needs for N particles.
-size_t filter_smem_bytes(int N, int U, int block_threads);
+// Bytes of the particle population of one filter: N (8 + 4U + 4) bytes, plus
+// 4N for the ancestors when the digest is requested.
+size_t filter_smem_bytes(int N, int U, bool digest);
 
 // Largest reaction-count template that fits R.
 int reaction_tier(int R);
