@@ -37,6 +37,8 @@ namespace dev {
 
 
 constexpr int kMaxWarps = 32;
+constexpr int kMaxRemnants = 128;  // >= block size
+constexpr int kParkLanes = 16;      // a warp below this many busy lanes parks its particles
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kResampleLane = 0xFFFFFFFFu;
 
@@ -52,6 +54,10 @@ struct SharedHead {
     int status;
     int valid;
     int pool_next;
+    int rem_n[2];                        // parked particles per list
+    int rem_j[2][kMaxRemnants];          // parked particle index
+    uint32_t rem_draws[2][kMaxRemnants]; // its draw counter
+    double rem_t[2][kMaxRemnants];       // its time
     int bucket[16];
     float rate_f[PF_MAX_REACTIONS];  // FP32 copy of rate[], for cost estimates only
     LogTab logt;
@@ -123,93 +129,145 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
     Lane<UM> L;
     L.xs = xs;
     L.Np = Np;
-    auto take = [&](bool &act) {
-        const int slot = atomicAdd(&sh.pool_next, 1);
-        act = slot < N;
-        L.j = act ? order[slot] : 0;
+    auto load_x = [&](bool act) {
         if constexpr (UM > 0) {
 #pragma unroll
             for (int u = 0; u < UM; ++u) L.x[u] = (act && u < U) ? xs[u * Np + L.j] : 0;
         }
     };
+    auto store_x = [&]() {
+        if constexpr (UM > 0) {
+#pragma unroll
+            for (int u = 0; u < UM; ++u)
+                if (u < U) xs[u * Np + L.j] = L.x[u];
+        }
+    };
+    auto take = [&](bool &act) {
+        const int slot = atomicAdd(&sh.pool_next, 1);
+        act = slot < N;
+        L.j = act ? order[slot] : 0;
+        load_x(act);
+    };
     double a[RM], S[RM];
 #pragma unroll
     for (int r = 0; r < RM; ++r) a[r] = 0.0;
-    bool active;
-    take(active);
-    double t = t_prev;
-    uint32_t draws = 0;
-    uint32_t mask = all;  // propensities to (re)compute before the next step
-    while (__any_sync(kFull, active)) {
-        if (!active) continue;
-#pragma unroll
-        for (int r = 0; r < RM; ++r)
-            if ((mask >> r) & 1u) a[r] = propensity<UM>(r, sh, L);
-        double run = a[0];
-        S[0] = run;
-#pragma unroll
-        for (int r = 1; r < RM; ++r) {
-            if (r < R) run = __dadd_rn(run, a[r]);
-            S[r] = run;
-        }
-        const double a0 = run;
-        bool done;
-        if (dbits(a0) == 0) {
-            done = true;                                   // absorbing: nothing can fire
-        } else if (draws >= budget) {
-            sh.status = PF_ST_BUDGET;
-            done = true;
-        } else {
-            const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
-                                            key1);
-            ++draws;
-            const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
-            const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
-            // tau = -log(u1) / a0 with u1 = ((r0 >> 11) + 1) 2^-53 in (0, 1]
-            const double tau = __ddiv_rn(neg_log_u53((r0 >> 11) + 1ull, sh.logt), a0);
-            const double t_next = __dadd_rn(t, tau);
-            if (dbits(t_next) > t_end_bits) {
-                done = true;                               // the event lies past t_end
-            } else {
-                const uint64_t v2 = r1 >> 11;              // u2 = v2 2^-53 in [0, 1)
-                const double target = __dmul_rn(v2 ? scaled_u53(v2) : 0.0, a0);
-                const long long tb = dbits(target);
-                int chosen = 0;                            // first r with target < S_r
-#pragma unroll
-                for (int r = 0; r < RM; ++r) chosen += (r < R && dbits(S[r]) <= tb) ? 1 : 0;
-                if (chosen >= R) {                         // rounding guard
-                    chosen = 0;
-#pragma unroll
-                    for (int r = 0; r < RM; ++r)
-                        if (r < R && dbits(a[r]) != 0) chosen = r;
-                }
-                const int nch = sh.net.n_change[chosen];
-                for (int i = 0; i < nch; ++i) {
-                    const int sp = sh.net.ch_sp[chosen][i], dlt = sh.net.ch_delta[chosen][i];
-                    if constexpr (UM > 0) {
-#pragma unroll
-                        for (int u = 0; u < UM; ++u) L.x[u] += (sp == u) ? dlt : 0;
-                    } else {
-                        xs[sp * Np + L.j] += dlt;
-                    }
-                }
-                t = t_next;
-                ++fired;
-                mask = sh.net.dep[chosen];
-                done = false;
-            }
-        }
-        if (done) {
-            if constexpr (UM > 0) {
-#pragma unroll
-                for (int u = 0; u < UM; ++u)
-                    if (u < U) xs[u * Np + L.j] = L.x[u];
-            }
+    // Rounds: the first draws particles from the pool; when the pool is empty,
+    // warps whose busy lanes fall below kParkLanes park their particles (exact
+    // state: index, time, draw counter) and all warps meet at a barrier; the
+    // parked particles are repacked onto the first lanes of the block and the
+    // next round continues them, until none is left.
+    int src = 0, remaining = N;
+    bool first = true;
+    for (;;) {
+        bool active;
+        double t;
+        uint32_t draws;
+        if (first) {
             take(active);
             t = t_prev;
             draws = 0;
-            mask = all;
+        } else {
+            active = static_cast<int>(threadIdx.x) < remaining;
+            L.j = active ? sh.rem_j[src][threadIdx.x] : 0;
+            t = active ? sh.rem_t[src][threadIdx.x] : t_prev;
+            draws = active ? sh.rem_draws[src][threadIdx.x] : 0u;
+            load_x(active);
         }
+        const int dst = src ^ 1;
+        const bool may_park = remaining > 32;
+        uint32_t mask = all;  // propensities to (re)compute before the next step
+        for (;;) {
+            const unsigned busy = __ballot_sync(kFull, active);
+            if (busy == 0) break;
+            if (may_park && __popc(busy) < kParkLanes &&
+                *reinterpret_cast<volatile int *>(&sh.pool_next) >= N) {
+                if (active) {
+                    const int slot = atomicAdd(&sh.rem_n[dst], 1);
+                    sh.rem_j[dst][slot] = L.j;
+                    sh.rem_t[dst][slot] = t;
+                    sh.rem_draws[dst][slot] = draws;
+                    store_x();
+                }
+                break;
+            }
+            if (!active) continue;
+#pragma unroll
+            for (int r = 0; r < RM; ++r)
+                if ((mask >> r) & 1u) a[r] = propensity<UM>(r, sh, L);
+            double run = a[0];
+            S[0] = run;
+#pragma unroll
+            for (int r = 1; r < RM; ++r) {
+                if (r < R) run = __dadd_rn(run, a[r]);
+                S[r] = run;
+            }
+            const double a0 = run;
+            bool done;
+            if (dbits(a0) == 0) {
+                done = true;                                   // absorbing: nothing can fire
+            } else if (draws >= budget) {
+                sh.status = PF_ST_BUDGET;
+                done = true;
+            } else {
+                const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow,
+                                                key0, key1);
+                ++draws;
+                const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+                const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
+                // tau = -log(u1) / a0 with u1 = ((r0 >> 11) + 1) 2^-53 in (0, 1]
+                const double tau = __ddiv_rn(neg_log_u53((r0 >> 11) + 1ull, sh.logt), a0);
+                const double t_next = __dadd_rn(t, tau);
+                if (dbits(t_next) > t_end_bits) {
+                    done = true;                               // the event lies past t_end
+                } else {
+                    const uint64_t v2 = r1 >> 11;              // u2 = v2 2^-53 in [0, 1)
+                    const double target = __dmul_rn(v2 ? scaled_u53(v2) : 0.0, a0);
+                    const long long tb = dbits(target);
+                    int chosen = 0;                            // first r with target < S_r
+#pragma unroll
+                    for (int r = 0; r < RM; ++r) chosen += (r < R && dbits(S[r]) <= tb) ? 1 : 0;
+                    if (chosen >= R) {                         // rounding guard
+                        chosen = 0;
+#pragma unroll
+                        for (int r = 0; r < RM; ++r)
+                            if (r < R && dbits(a[r]) != 0) chosen = r;
+                    }
+                    const int nch = sh.net.n_change[chosen];
+                    for (int i = 0; i < nch; ++i) {
+                        const int sp = sh.net.ch_sp[chosen][i], dlt = sh.net.ch_delta[chosen][i];
+                        if constexpr (UM > 0) {
+#pragma unroll
+                            for (int u = 0; u < UM; ++u) L.x[u] += (sp == u) ? dlt : 0;
+                        } else {
+                            xs[sp * Np + L.j] += dlt;
+                        }
+                    }
+                    t = t_next;
+                    ++fired;
+                    mask = sh.net.dep[chosen];
+                    done = false;
+                }
+            }
+            if (done) {
+                store_x();
+                if (first) {
+                    take(active);
+                } else {
+                    active = false;
+                }
+                t = t_prev;
+                draws = 0;
+                mask = all;
+            }
+        }
+        __syncthreads();
+        remaining = sh.rem_n[dst];
+        if (remaining == 0) break;
+        // the list consumed now receives the next round's parked particles
+        if (threadIdx.x == 0) sh.rem_n[src] = 0;
+        __syncthreads();
+        src = dst;
+        first = false;
     }
 }
 
@@ -464,6 +522,8 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
                     run += c;
                 }
                 sh.pool_next = 0;
+                sh.rem_n[0] = 0;
+                sh.rem_n[1] = 0;
             }
             __syncthreads();
             for (int j = tid; j < N; j += B)
