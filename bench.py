@@ -44,11 +44,17 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = FP64_FLOPS_PER_SM_CLK * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
 # FP64 flops (FMA = 2) of the two transcendental steps of an SSA event, as the
 # library computes them, counted by ncu's FP64 instruction counters on the
-# pf_fp64_probe kernels: the table-driven -log(u) is 1 DADD + 2 DMUL +
-# 6 DFMA + 2 DADD (= 17 flops, 11 operations); the IEEE division is
-# 7 DFMA + 1 DMUL (= 15 flops, 8 operations).
-FP64_FLOPS_LOG, FP64_OPS_LOG = 17.0, 11.0
+# pf_fp64_probe kernels: the table-driven -log(u) is 4 DADD + 2 DMUL +
+# 6 DFMA (= 18 flops, 12 operations); the IEEE division is 7 DFMA + 1 DMUL
+# (= 15 flops, 8 operations).
+FP64_FLOPS_LOG, FP64_OPS_LOG = 18.0, 12.0
 FP64_FLOPS_DIV, FP64_OPS_DIV = 15.0, 8.0
+
+
+# DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression
+# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on the 152-theta
+# case of the same kernel (0.709 MB) scaled by the filters processed (x 4096/152).
+FILTER_TRAFFIC_BYTES = 19.1e6
 
 
 def flops_per_event(R: int) -> float:
@@ -355,7 +361,7 @@ def main() -> None:
             "gpu_launches": 2 * a.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None,
+                         "traffic": FILTER_TRAFFIC_BYTES if w.name == WORKLOAD and w.M == 4096 else None,
                          "kernel": "filter_kernel (FP64 pipe)",
                          "flops_per_event": fpe,
                          "fp64_ops_per_event": ops_per_event(w.R),
