@@ -259,12 +259,11 @@ def main() -> None:
         run_pattern(a)
         return
 
+    from paper_1606_08281_gb300 import multi
     w = W.get(a.workload)
     if a.max_theta:
         w.M = min(w.M, a.max_theta)
-    th_np = w.thetas() if rank == 0 else W.log_uniform(
-        np.random.default_rng(w.theta_seed + 7919 * rank), w.prior_lo, w.prior_hi, w.M)
-    th_np = np.ascontiguousarray(th_np[: w.M])
+    th_np = np.ascontiguousarray(multi.rank_thetas(w, rank)[: w.M])
     y_np = w.observations()
     th = torch.from_numpy(th_np).to(dev)
     yd = torch.from_numpy(y_np).to(dev)
@@ -306,13 +305,9 @@ def main() -> None:
     torch.cuda.synchronize()
     clk = clocks.stop()
     local_ms = float(np.mean(times))
+    ms = multi.max_over_ranks(local_ms, dev)
     if world > 1:
-        t = torch.tensor([local_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        ms = float(t.item())
-    else:
-        ms = local_ms
 
     # end to end through the C ABI with host (pinned) buffers
     th_pin = torch.from_numpy(th_np).pin_memory()
@@ -330,11 +325,7 @@ def main() -> None:
         e2e_times.append(time.perf_counter() - t0)
     if e2e_times:
         assert np.array_equal(host_out["loglik"], out["loglik"].cpu().numpy())
-    e2e_s = float(np.mean(e2e_times)) if e2e_times else float("nan")
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = multi.max_over_ranks(float(np.mean(e2e_times)) if e2e_times else float("nan"), dev)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
