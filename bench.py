@@ -232,6 +232,8 @@ def main() -> None:
                          "heterogeneous request mix vs plain per-request launches; serve: a "
                          "Poisson request stream, continuous batching vs a plain FIFO server")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--autotune", action="store_true",
+                    help="tune block size and launch order on a theta sample before timing")
     a = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -274,9 +276,16 @@ def main() -> None:
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
+    launch = {"block_threads": 0, "schedule": pf.PF_SCHED_AUTO}
+    if a.autotune:
+        from paper_1606_08281_gb300 import autotune
+        tuned = autotune.tune(w.net, th_np, w.x0, w.obs_times, y_np, w.C, w.sigma, w.N,
+                              sample_filters=20 * 608, cache=None)
+        launch = {"block_threads": tuned["block_threads"], "schedule": tuned["schedule"]}
+
     def step():
         pf.pf_loglik(w.net, th, w.x0, w.obs_times, yd, w.C, w.sigma, w.N, w.filter_seed,
-                     out=out, stream=stream.cuda_stream)
+                     out=out, stream=stream.cuda_stream, **launch)
 
     for _ in range(a.warmup):
         step()
@@ -343,7 +352,7 @@ def main() -> None:
             "metric": "theta-likelihoods/s", "value": value, "unit": "theta-likelihoods/s",
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config_of(w),
+            "data": "synthetic", "config": {**config_of(w), "launch": launch},
             "ssa_events_per_s": world * ev_step / (ms * 1e-3),
             "events_per_step": ev_step,
             "clocks": clk,
