@@ -58,6 +58,9 @@ extern "C" {
 #define PF_ST_NONFINITE 2     /* a weight was not finite; loglik = -inf       */
 #define PF_ST_INVALID_THETA 3 /* theta row has a negative or non-finite entry;
                                  loglik = NaN, nothing was simulated          */
+#define PF_ST_REJECTED 4      /* early rejection was requested and the row's
+                                 log-likelihood is certainly below the
+                                 threshold; loglik = -inf                     */
 
 /* ---- limits ------------------------------------------------------------ */
 #define PF_MAX_SPECIES 16
@@ -112,6 +115,18 @@ typedef struct {
  *   row_order     optional [M] permutation of 0..M-1 (same memory space as
  *                 thetas): the theta rows in the order their filters are
  *                 launched; overrides `schedule`.
+ *   early_reject  1: stop a theta row as soon as its log-likelihood is
+ *                 certainly below reject_below (the level-set threshold
+ *                 log epsilon_k of Alg. 2, whose acceptance test keeps theta
+ *                 only if l_hat(theta) >= epsilon_k) and report it as
+ *                 PF_ST_REJECTED.  Every per-time-point factor of the filter
+ *                 is at most prod_p 1/(sigma_p sqrt(2 pi)), so the sum of the
+ *                 trajectories' running log-likelihoods plus that bound for the
+ *                 remaining time points bounds the final value from above.
+ *                 Rows not rejected get exactly the values computed without
+ *                 the threshold; which rows are rejected does not depend on
+ *                 the launch (up to rounding of the running sum, ~1e-12
+ *                 relative, for a row whose value equals the threshold).
  *   Diagnostics are defined only for filters whose status is PF_ST_OK.
  */
 #define PF_SCHED_AUTO 0
@@ -127,8 +142,9 @@ typedef struct {
     uint64_t *digest;
     int32_t *final_states;
     int32_t schedule;
-    int32_t reserved;
+    int32_t early_reject;
     const uint32_t *row_order;
+    double reject_below;
 } pf_options;
 
 /*
@@ -234,8 +250,9 @@ int pf_ctx_load_problem(pf_ctx *ctx, const pf_network *net, int32_t d, const int
 /* One request: host arrays, read at submission (theta) and written at
  * completion (loglik/status; status may be NULL).  K_use = number of leading
  * observation times to use (0 = all of the problem's).  event_budget 0 =
- * default.  loglik_threshold is carried for the caller's bookkeeping (the
- * level-set threshold epsilon_k of Alg. 2); it does not change the result. */
+ * default.  loglik_threshold: the level-set threshold log epsilon_k of
+ * Alg. 2; when finite, rows certainly below it stop early with
+ * PF_ST_REJECTED (as pf_options.early_reject); NaN = evaluate every row fully. */
 typedef struct {
     int32_t problem_id;
     int32_t d;

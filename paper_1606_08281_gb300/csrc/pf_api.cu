@@ -278,6 +278,16 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
         grid = (int)std::min<int64_t>(F, pf::global_grid(sms));
         PF_CUDA(b_slab.alloc(smem * (size_t)grid, s), "alloc global populations");
     }
+    DevBuf b_acc;
+    if (o.early_reject) {
+        if (std::isnan(o.reject_below)) return fail(PF_EINVAL, "early_reject needs a reject_below value");
+        PF_CUDA(b_acc.alloc(sizeof(double) * M, s), "alloc rejection bounds");
+        a.slack = pf::increment_slack(a.net);
+        a.reject_below = o.reject_below;
+        a.acc = (double *)b_acc.p;
+        int ef = pf::launch_fill(a.acc, M, (double)T * K * a.slack, s);
+        if (ef) return cuda_fail((cudaError_t)ef, "fill rejection bounds");
+    }
     int e = pf::launch_filter(a, B, d_ll, d_st, s, (unsigned char *)b_slab.p, smem, grid);
     if (e) return cuda_fail((cudaError_t)e, "filter launch");
 

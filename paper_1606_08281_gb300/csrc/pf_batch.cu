@@ -60,6 +60,10 @@ struct RequestDev {
     int64_t row_base;         // first row of the slot's output arena
     uint64_t seed, budget;
     int32_t d, N, K, T;
+    double *acc;              // this request's rejection bounds (row_base-relative), or null
+    double reject_below;
+    double slack;
+    double acc_init;          // T * K * slack
 };
 
 struct BatchHeader {
@@ -72,6 +76,17 @@ struct BatchHeader {
 
 __global__ void reset_kernel(unsigned long long *counters) {
     if (threadIdx.x < kGroups) counters[threadIdx.x] = 0ull;
+}
+
+// Starting value of the early-rejection bound of every row whose request has a
+// threshold.
+__global__ void init_bounds_kernel(const BatchHeader *hdr, const RequestDev *reqs) {
+    const int nreq = hdr->n_requests;
+    for (int r = blockIdx.x; r < nreq; r += gridDim.x) {
+        const RequestDev &q = reqs[r];
+        if (!q.acc) continue;
+        for (int64_t m = threadIdx.x; m < q.M; m += blockDim.x) q.acc[m] = q.acc_init;
+    }
 }
 
 template <int RM, int UM, bool GLOBAL>
@@ -128,6 +143,9 @@ batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *ite
         job.ev_out = ev_f + f;
         job.dg_out = nullptr;
         job.fs_out = nullptr;
+        job.acc = rq.acc ? rq.acc + row : nullptr;
+        job.reject_below = rq.reject_below;
+        job.slack = rq.slack;
         run_filter<RM, UM>(job, sh, arrays);
     }
 }
@@ -236,6 +254,7 @@ struct Slot {
     uint8_t *st_f = nullptr;
     unsigned long long *ev_f = nullptr;
     unsigned long long *counters = nullptr;
+    double *acc = nullptr;              // [cap_rows] rejection bounds
     unsigned char *slab[kGroups] = {};
     int grid[kGroups] = {};
     size_t smem[kGroups] = {};
@@ -297,6 +316,7 @@ void free_slot(Slot &s) {
     if (s.st_f) cudaFree(s.st_f);
     if (s.ev_f) cudaFree(s.ev_f);
     if (s.counters) cudaFree(s.counters);
+    if (s.acc) cudaFree(s.acc);
 }
 
 template <typename T>
@@ -328,6 +348,7 @@ int init_slot(pf_ctx *ctx, int si) {
     CTX_CUDA(cudaMalloc(&s.st_f, ctx->cap_items), "scratch");
     CTX_CUDA(cudaMalloc(&s.ev_f, sizeof(unsigned long long) * ctx->cap_items), "scratch");
     CTX_CUDA(cudaMalloc(&s.counters, sizeof(unsigned long long) * kGroups), "counters");
+    CTX_CUDA(cudaMalloc(&s.acc, sizeof(double) * ctx->cap_rows), "rejection bounds");
     int sms = 0;
     CTX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "attr");
     for (int g = 0; g < kGroups; ++g) {
@@ -349,6 +370,7 @@ int init_slot(pf_ctx *ctx, int si) {
     // capture: reset -> persistent group kernels (forked) -> reduce
     CTX_CUDA(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal), "capture");
     reset_kernel<<<1, 32, 0, s.stream>>>(s.counters);
+    init_bounds_kernel<<<sms, 256, 0, s.stream>>>(s.hdr_d, s.req_d);
     cudaEventRecord(s.fork, s.stream);
     for (int g = 0; g < kGroups; ++g) {
         cudaStreamWaitEvent(s.side[g], s.fork, 0);
@@ -433,6 +455,17 @@ int launch_batch(pf_ctx *ctx, int si, const std::vector<ReqState *> &batch) {
         rd.N = r.n_particles;
         rd.K = r.K_use;
         rd.T = p.T;
+        if (std::isfinite(r.loglik_threshold)) {
+            rd.acc = s.acc + rows;
+            rd.reject_below = r.loglik_threshold;
+            rd.slack = increment_slack(p.net);
+            rd.acc_init = static_cast<double>(p.T) * r.K_use * rd.slack;
+        } else {
+            rd.acc = nullptr;
+            rd.reject_below = 0.0;
+            rd.slack = 0.0;
+            rd.acc_init = 0.0;
+        }
         st->row_base = rows;
         st->slot = si;
         rows += r.M;

@@ -401,6 +401,14 @@ struct FilterJob {
     unsigned long long *ev_out;
     unsigned long long *dg_out;  // may be null
     int32_t *fs_out;             // [N][U], may be null
+    // Early rejection (level-set threshold): acc points at this theta row's
+    // running upper bound of its log-likelihood, shared by its trajectories'
+    // filters (null: off).  Each interval adds (increment - slack), where
+    // slack >= 0 bounds every increment from above; the filter stops with
+    // PF_ST_REJECTED once the bound is below reject_below.
+    double *acc;
+    double reject_below;
+    double slack;
 };
 
 template <int RM, int UM>
@@ -464,6 +472,12 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
 
     for (int k = 0; k < K; ++k) {
         const uint32_t lane = (static_cast<uint32_t>(traj) << 20) | static_cast<uint32_t>(k);
+        if (job.acc) {  // another trajectory of this theta may already have pushed the bound below
+            if (tid == 0 && *reinterpret_cast<volatile double *>(job.acc) < job.reject_below)
+                sh.status = PF_ST_REJECTED;
+            __syncthreads();
+            if (sh.status != PF_ST_OK) break;
+        }
         if (k > 0) {
             // systematic resampling on the integer weights of interval k-1
             block_scan_u64(qbuf, N, sh);
@@ -575,6 +589,11 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
             inc = __dsub_rn(inc, log(static_cast<double>(N)));
             inc = __dsub_rn(inc, sh.lognorm);
             sh.ll = __dadd_rn(sh.ll, inc);
+            if (job.acc) {
+                const double add = __dsub_rn(inc, job.slack);
+                if (__dadd_rn(atomicAdd(job.acc, add), add) < job.reject_below)
+                    sh.status = PF_ST_REJECTED;
+            }
         }
         t_prev = t_k;
     }

@@ -23,6 +23,7 @@
 // where CUDA's log/exp differ from another libm in the last place.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -68,6 +69,9 @@ __global__ void __launch_bounds__(128, 4) filter_kernel(const FilterArgs args) {
     job.dg_out = args.dg_f ? reinterpret_cast<unsigned long long *>(args.dg_f) + f : nullptr;
     job.fs_out = args.final_states ? args.final_states + f * static_cast<int64_t>(args.N) * args.net.U
                                    : nullptr;
+    job.acc = args.acc ? args.acc + mrow : nullptr;
+    job.reject_below = args.reject_below;
+    job.slack = args.slack;
     run_filter<RM, UM>(job, sh, smem);
 }
 
@@ -112,6 +116,9 @@ __global__ void __launch_bounds__(128, 4) filter_kernel_global(const FilterArgs 
         job.fs_out = args.final_states
                          ? args.final_states + f * static_cast<int64_t>(args.N) * args.net.U
                          : nullptr;
+        job.acc = args.acc ? args.acc + mrow : nullptr;
+        job.reject_below = args.reject_below;
+        job.slack = args.slack;
         run_filter<RM, UM>(job, sh, arrays);
     }
 }
@@ -241,6 +248,12 @@ __global__ void __launch_bounds__(1024) order_kernel(const uint32_t *cost, int64
         order[atomicAdd(&hist[bucket(cost[m])], 1)] = static_cast<uint32_t>(m);
 }
 
+__global__ void fill_kernel(double *p, int64_t n, double v) {
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        p[i] = v;
+}
+
 __global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n) {
     const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -322,6 +335,22 @@ int launch_schedule(const FilterArgs &a, uint32_t *cost, uint32_t *order, uint32
     if (e != cudaSuccess) return e;
     order_kernel<<<1, 1024, 0, s>>>(cost, a.M, order);
     return cudaGetLastError();
+}
+
+int launch_fill(double *p, int64_t n, double value, void *stream) {
+    if (n == 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 4096);
+    fill_kernel<<<static_cast<unsigned>(blocks), 256, 0, static_cast<cudaStream_t>(stream)>>>(p, n, value);
+    return cudaGetLastError();
+}
+
+double increment_slack(const NetTables &t) {
+    double lognorm = 0.0;
+    for (int p = 0; p < t.P; ++p) lognorm += std::log(t.sigma[p]);
+    lognorm += 0.5 * t.P * std::log(2.0 * M_PI);
+    // a positive bound is enlarged by a relative 1e-9 so that it stays an upper
+    // bound whatever the last-place differences of the device's logarithm
+    return lognorm >= 0.0 ? 0.0 : -lognorm * (1.0 + 1e-9);
 }
 
 int launch_philox(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,

@@ -42,6 +42,9 @@ struct FilterArgs {
     uint64_t *dg_f;          // may be null: digest not computed
     int32_t *final_states;   // [M*T][N][U], may be null
     const uint32_t *row_order;  // [M] theta rows in launch order (null: 0..M-1)
+    double *acc;                // [M] running upper bounds for early rejection (null: off)
+    double reject_below;
+    double slack;               // upper bound of one per-time-point log increment, >= 0
 };
 
 // Bytes of the particle population of one filter: N (8 + 4U + 4) bytes, plus
@@ -61,6 +64,13 @@ int launch_filter(const FilterArgs &a, int block_threads, double *loglik, uint8_
 
 // Resident blocks for the global-memory variant on a GPU with `sms` SMs.
 int global_grid(int sms);
+
+// p[0..n) = value on `stream`.
+int launch_fill(double *p, int64_t n, double value, void *stream);
+
+// Upper bound >= 0 of one per-time-point log-likelihood increment of the
+// filter: max(0, -sum_p log sigma_p - (P/2) log 2 pi), rounded up.
+double increment_slack(const NetTables &t);
 
 // Heaviest-first launch order of the theta rows: a pilot kernel simulates
 // one unconditioned path per row over [0, t_K] (its own random stream, at most

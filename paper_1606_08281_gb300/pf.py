@@ -23,7 +23,7 @@ _lock = threading.Lock()
 
 PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT, PF_EAGAIN, PF_ENOTFOUND, PF_EBUSY = (
     0, -1, -2, -3, -4, -5, -6, -7)
-PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA = 0, 1, 2, 3
+PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA, PF_ST_REJECTED = 0, 1, 2, 3, 4
 PF_SCHED_AUTO, PF_SCHED_NATURAL, PF_SCHED_HEAVY_FIRST = 0, 1, 2
 
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
@@ -56,8 +56,9 @@ class pf_options(ct.Structure):
     _fields_ = [("event_budget", ct.c_uint64), ("device_ptrs", ct.c_int32),
                 ("block_threads", ct.c_int32), ("stream", ct.c_void_p),
                 ("ll_traj", ct.c_void_p), ("events", ct.c_void_p), ("digest", ct.c_void_p),
-                ("final_states", ct.c_void_p), ("schedule", ct.c_int32), ("reserved", ct.c_int32),
-                ("row_order", ct.c_void_p)]
+                ("final_states", ct.c_void_p), ("schedule", ct.c_int32),
+                ("early_reject", ct.c_int32), ("row_order", ct.c_void_p),
+                ("reject_below", ct.c_double)]
 
 
 def library_path() -> Path:
@@ -159,7 +160,7 @@ def _is_torch_cuda(x) -> bool:
 def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, seed: int, *,
               event_budget: int = 0, block_threads: int = 0, stream=None,
               diagnostics: bool = False, final_states: bool = False, out=None,
-              schedule: int = PF_SCHED_AUTO, row_order=None):
+              schedule: int = PF_SCHED_AUTO, row_order=None, reject_below=None):
     """Log-likelihood of every theta row (see pf_loglik in include/pf1606.h).
 
     Returns a dict with 'loglik' [M] and 'status' [M]; with diagnostics=True
@@ -225,7 +226,8 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
         p_ro = _hptr(ro)
     opt = pf_options(int(event_budget), 1 if device else 0, int(block_threads),
                      stream if device else None, ptr("ll_traj"), ptr("events"), ptr("digest"),
-                     ptr("final_states"), int(schedule), 0, p_ro)
+                     ptr("final_states"), int(schedule), 0 if reject_below is None else 1, p_ro,
+                     float("nan") if reject_below is None else float(reject_below))
     rc = lib.pf_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), p_ts, K, p_y, T, P, _hptr(Ch),
                        _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
                        ptr("loglik"), ptr("status"), ct.byref(opt))

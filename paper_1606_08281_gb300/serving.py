@@ -32,8 +32,28 @@ def _load_problems(ctx, names):
 
 def _plain(spec, w):
     K = spec.K_use
+    thr = spec.threshold if np.isfinite(spec.threshold) else None
     return pf.pf_loglik(w.net, spec.thetas, w.x0, w.obs_times[:K], w.observations()[:, :K, :],
-                        w.C, w.sigma, spec.n_particles, spec.seed)
+                        w.C, w.sigma, spec.n_particles, spec.seed, reject_below=thr)
+
+
+def calibrate_thresholds(stream, rows: int = 256) -> dict:
+    """Level-set threshold per network: the median log-likelihood (alpha = 50 %)
+    of the first `rows` theta rows of that network's requests, evaluated fully
+    once before the stream starts -- the sampler's quantile rule for epsilon_k."""
+    out = {}
+    for name in sorted({s.problem for s in stream}):
+        specs = [s for s in stream if s.problem == name]
+        th = np.concatenate([s.thetas for s in specs])[:rows]
+        s0 = specs[0]
+        w = W.get(name)
+        K = s0.K_use
+        r = pf.pf_loglik(w.net, th, w.x0, w.obs_times[:K], w.observations()[:, :K, :], w.C,
+                         w.sigma, s0.n_particles, 12345)
+        out[name] = float(np.median(r["loglik"]))
+    for s in stream:
+        s.threshold = out[s.problem]
+    return out
 
 
 def run_hetero(mix, n_slots: int = 3, repeats: int = 1) -> dict:
@@ -138,9 +158,13 @@ def serve_plain(stream) -> dict:
     return {"theta_per_s": rows / span, "span_s": span, **_percentiles(lat), "loglik": outs}
 
 
-def run_serving(stream, n_slots: int = 3) -> dict:
+def run_serving(stream, n_slots: int = 3, thresholds: bool = True) -> dict:
+    thr = calibrate_thresholds(stream) if thresholds else {}
     b = serve_batched(stream, n_slots)
     p = serve_plain(stream)
-    same = all(np.array_equal(x, y) for x, y in zip(b.pop("loglik"), p.pop("loglik")))
+    lb, lp = b.pop("loglik"), p.pop("loglik")
+    same = all(np.array_equal(x, y) for x, y in zip(lb, lp))
+    rejected = int(sum(np.isneginf(x).sum() for x in lb))
     return {"requests": len(stream), "theta_rows": int(sum(len(s.thetas) for s in stream)),
+            "thresholds": thr, "rejected_rows": rejected,
             "batched": b, "plain": p, "identical_results": bool(same)}

@@ -143,3 +143,20 @@ def test_bad_requests(pf, ctx, problems):
         pf.pf_submit(ctx, pf.Request(pid, np.ones((1, 2)), 10, 1, K_use=999))
     with pytest.raises(pf.PfError):
         pf.pf_submit(ctx, pf.Request(pid, np.ones((1, 2)), 100000, 1))
+
+
+def test_batch_early_rejection_matches_plain(pf, ctx, problems):
+    """Requests carrying a level-set threshold: the context rejects exactly the
+    rows the plain call rejects, and keeps the others' values."""
+    pid, w = problems["gene_expression"]
+    th = W.log_uniform(np.random.default_rng(77), w.prior_lo, w.prior_hi, 40)
+    full = plain(pf, w, th, 200, 5, 10)
+    thr = float(np.median(full["loglik"]))
+    reqs = [pf.Request(pid, th, 200, 5, K_use=10, loglik_threshold=thr),
+            pf.Request(problems["birth_death"][0], problems["birth_death"][1].thetas(8), 50, 6)]
+    pf.pf_ctx_run_batch(ctx, reqs)
+    ref = pf.pf_loglik(w.net, th, w.x0, w.obs_times[:10], w.observations()[:, :10, :], w.C,
+                       w.sigma, 200, 5, reject_below=thr)
+    assert (reqs[0].status == ref["status"]).all()
+    assert np.array_equal(reqs[0].loglik, ref["loglik"])
+    assert (reqs[0].status == pf.PF_ST_REJECTED).sum() == (full["loglik"] < thr).sum()

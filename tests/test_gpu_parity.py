@@ -201,6 +201,30 @@ def test_schedule_does_not_change_results(pf):
     assert (a["events"] == b["events"]).all()
 
 
+@pytest.mark.parametrize("case", ["gene_expression", "birth_death_small_sigma"])
+def test_early_rejection_matches_full_evaluation(pf, case):
+    """With the level-set threshold at the median, rows whose full log-likelihood
+    is below it are REJECTED (-inf) and every other row keeps exactly its full
+    value.  The small-sigma case has positive per-interval bounds (slack)."""
+    if case == "gene_expression":
+        w = W.gene_expression().subset(T=3, K=12)
+        th, N, sigma = w.thetas(64), 300, w.sigma
+    else:
+        w = W.birth_death()
+        th, N, sigma = w.thetas(64), 64, np.array([0.2])
+    full = pf.pf_loglik(w.net, th, w.x0, w.obs_times, w.observations(), w.C, sigma, N, 31,
+                        diagnostics=True)
+    thr = float(np.median(full["loglik"]))
+    cut = pf.pf_loglik(w.net, th, w.x0, w.obs_times, w.observations(), w.C, sigma, N, 31,
+                       diagnostics=True, reject_below=thr)
+    below = full["loglik"] < thr
+    assert (cut["status"][below] == pf.PF_ST_REJECTED).all()
+    assert np.isneginf(cut["loglik"][below]).all()
+    assert (cut["status"][~below] == 0).all()
+    assert np.array_equal(cut["loglik"][~below], full["loglik"][~below])
+    assert cut["events"].sum() < full["events"].sum()       # rejected rows stopped early
+
+
 def test_repeatable(pf):
     w = W.gene_expression().subset(T=2, K=10)
     a = pf.pf_loglik(w.net, w.thetas(32), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
