@@ -108,6 +108,22 @@ __device__ __forceinline__ double propensity(int r, const SharedHead &sh, const 
     return __dmul_rn(sh.rate[r], count_to_double(combos<UM>(r, sh.net, L)));
 }
 
+// Reactant description of reaction r packed in one word for register-resident
+// copies: (sp_a + 1) | ord_a << 8 | (sp_b + 1) << 16 | ord_b << 24.
+__device__ __forceinline__ int pack_reactants(const NetTables &n, int r) {
+    return (n.sp_a[r] + 1) | (n.ord_a[r] << 8) | ((n.sp_b[r] + 1) << 16) | (n.ord_b[r] << 24);
+}
+
+// propensity() from register copies of rate and the packed reactant word.
+template <int UM>
+__device__ __forceinline__ double propensity_reg(double rate, int desc, const Lane<UM> &L) {
+    const int sa = (desc & 0xFF) - 1, pa = (desc >> 8) & 0xFF;
+    const int sb = ((desc >> 16) & 0xFF) - 1, pb = (desc >> 24) & 0xFF;
+    long long h = sa >= 0 ? binom_small(L.get(sa), pa) : 1;
+    if (sb >= 0) h *= binom_small(L.get(sb), pb);
+    return __dmul_rn(rate, count_to_double(h));
+}
+
 // Bits of a non-negative double: for x, y >= +0, x <= y iff bits(x) <= bits(y)
 // as signed integers, so these compares run on the integer pipes.
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
@@ -151,6 +167,18 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
     double a[RM], S[RM];
 #pragma unroll
     for (int r = 0; r < RM; ++r) a[r] = 0.0;
+    // small networks keep rates and reactant words in registers for the whole
+    // interval (the loop's atomics would otherwise force shared reloads)
+    constexpr bool kHoist = RM <= 4 && UM > 0;
+    double rate_reg[kHoist ? RM : 1];
+    int desc_reg[kHoist ? RM : 1];
+    if constexpr (kHoist) {
+#pragma unroll
+        for (int r = 0; r < RM; ++r) {
+            rate_reg[r] = r < R ? sh.rate[r] : 0.0;
+            desc_reg[r] = r < R ? pack_reactants(sh.net, r) : 0;
+        }
+    }
     // Rounds: the first draws particles from the pool; when the pool is empty,
     // warps whose busy lanes fall below kParkLanes park their particles (exact
     // state: index, time, draw counter) and all warps meet at a barrier; the
@@ -192,8 +220,12 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
             }
             if (!active) continue;
 #pragma unroll
-            for (int r = 0; r < RM; ++r)
-                if ((mask >> r) & 1u) a[r] = propensity<UM>(r, sh, L);
+            for (int r = 0; r < RM; ++r) {
+                if ((mask >> r) & 1u) {
+                    if constexpr (kHoist) a[r] = propensity_reg<UM>(rate_reg[r], desc_reg[r], L);
+                    else a[r] = propensity<UM>(r, sh, L);
+                }
+            }
             double run = a[0];
             S[0] = run;
 #pragma unroll
