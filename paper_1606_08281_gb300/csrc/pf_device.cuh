@@ -221,7 +221,12 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
             if (!active) continue;
 #pragma unroll
             for (int r = 0; r < RM; ++r) {
-                if ((mask >> r) & 1u) {
+                // a zero-order reaction's propensity is its rate exactly (theta * 1.0):
+                // a warp-uniform test skips the multiply for it
+                const bool zero_order = kHoist ? (desc_reg[r] & 0xFF) == 0 : sh.net.sp_a[r] < 0;
+                if (zero_order) {
+                    if ((mask >> r) & 1u) a[r] = kHoist ? rate_reg[r] : sh.rate[r];
+                } else if ((mask >> r) & 1u) {
                     if constexpr (kHoist) a[r] = propensity_reg<UM>(rate_reg[r], desc_reg[r], L);
                     else a[r] = propensity<UM>(r, sh, L);
                 }
