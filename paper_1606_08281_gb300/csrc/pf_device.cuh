@@ -207,8 +207,10 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
         for (;;) {
             const unsigned busy = __ballot_sync(kFull, active);
             if (busy == 0) break;
-            if (may_park && __popc(busy) < kParkLanes &&
-                *reinterpret_cast<volatile int *>(&sh.pool_next) >= N) {
+            // lane 0's view of the pool counter, so that the whole warp decides alike
+            const int pool_now =
+                __shfl_sync(kFull, *reinterpret_cast<volatile int *>(&sh.pool_next), 0);
+            if (may_park && __popc(busy) < kParkLanes && pool_now >= N) {
                 if (active) {
                     const int slot = atomicAdd(&sh.rem_n[dst], 1);
                     sh.rem_j[dst][slot] = L.j;
