@@ -92,6 +92,9 @@ int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P,
                 if (net->reactants[r2 * U + u] > 0) mask |= 1u << r2;
         }
         t.dep[r] = mask;
+        t.n_dep[r] = 0;
+        for (int r2 = 0; r2 < R; ++r2)
+            if ((mask >> r2) & 1u) t.dep_list[r][t.n_dep[r]++] = (int8_t)r2;
     }
     for (int u = 0; u < U; ++u) {
         if (x0[u] < 0) return fail(PF_EINVAL, "x0[%d] = %d < 0", u, x0[u]);

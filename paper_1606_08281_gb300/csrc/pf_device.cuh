@@ -170,6 +170,10 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
     // small networks keep rates and reactant words in registers for the whole
     // interval (the loop's atomics would otherwise force shared reloads)
     constexpr bool kHoist = RM <= 4 && UM > 0;
+    // dependency lists for large networks (state in shared memory); `mask`
+    // then holds either `all` (refill) or the fired reaction's index, which
+    // cannot collide since 2^R - 1 >= R
+    constexpr bool kDepList = UM == 0 && RM >= 16;
     double rate_reg[kHoist ? RM : 1];
     int desc_reg[kHoist ? RM : 1];
     if constexpr (kHoist) {
@@ -221,24 +225,48 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 break;
             }
             if (!active) continue;
+            if constexpr (kDepList) {
+                // large networks: each lane recomputes only its own dependent
+                // reactions (a full refill when mask is `all`); a trip issues
+                // max-over-lanes(#dependents) multiplies instead of one per
+                // reaction any lane needs
+                if (mask == all) {
+                    for (int r = 0; r < R; ++r) a[r] = propensity<UM>(r, sh, L);
+                } else {
+                    const int c = static_cast<int>(mask);  // the fired reaction (see below)
+                    const int nd = sh.net.n_dep[c];
+                    for (int i = 0; i < nd; ++i) {
+                        const int r = sh.net.dep_list[c][i];
+                        a[r] = propensity<UM>(r, sh, L);
+                    }
+                }
+            } else {
 #pragma unroll
-            for (int r = 0; r < RM; ++r) {
-                // a zero-order reaction's propensity is its rate exactly (theta * 1.0):
-                // a warp-uniform test skips the multiply for it
-                const bool zero_order = kHoist ? (desc_reg[r] & 0xFF) == 0 : sh.net.sp_a[r] < 0;
-                if (zero_order) {
-                    if ((mask >> r) & 1u) a[r] = kHoist ? rate_reg[r] : sh.rate[r];
-                } else if ((mask >> r) & 1u) {
-                    if constexpr (kHoist) a[r] = propensity_reg<UM>(rate_reg[r], desc_reg[r], L);
-                    else a[r] = propensity<UM>(r, sh, L);
+                for (int r = 0; r < RM; ++r) {
+                    // a zero-order reaction's propensity is its rate exactly (theta * 1.0):
+                    // a warp-uniform test skips the multiply for it
+                    const bool zero_order = kHoist ? (desc_reg[r] & 0xFF) == 0 : sh.net.sp_a[r] < 0;
+                    if (zero_order) {
+                        if ((mask >> r) & 1u) a[r] = kHoist ? rate_reg[r] : sh.rate[r];
+                    } else if ((mask >> r) & 1u) {
+                        if constexpr (kHoist) a[r] = propensity_reg<UM>(rate_reg[r], desc_reg[r], L);
+                        else a[r] = propensity<UM>(r, sh, L);
+                    }
                 }
             }
             double run = a[0];
             S[0] = run;
+            if constexpr (kDepList) {
+                for (int r = 1; r < R; ++r) {
+                    run = __dadd_rn(run, a[r]);
+                    S[r] = run;
+                }
+            } else {
 #pragma unroll
-            for (int r = 1; r < RM; ++r) {
-                if (r < R) run = __dadd_rn(run, a[r]);
-                S[r] = run;
+                for (int r = 1; r < RM; ++r) {
+                    if (r < R) run = __dadd_rn(run, a[r]);
+                    S[r] = run;
+                }
             }
             const double a0 = run;
             bool done;
@@ -263,13 +291,22 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                     const double target = __dmul_rn(v2 ? scaled_u53(v2) : 0.0, a0);
                     const long long tb = dbits(target);
                     int chosen = 0;                            // first r with target < S_r
+                    if constexpr (kDepList) {
+                        for (int r = 0; r < R; ++r) chosen += dbits(S[r]) <= tb ? 1 : 0;
+                        if (chosen >= R) {                     // rounding guard
+                            chosen = 0;
+                            for (int r = 0; r < R; ++r)
+                                if (dbits(a[r]) != 0) chosen = r;
+                        }
+                    } else {
 #pragma unroll
-                    for (int r = 0; r < RM; ++r) chosen += (r < R && dbits(S[r]) <= tb) ? 1 : 0;
-                    if (chosen >= R) {                         // rounding guard
-                        chosen = 0;
+                        for (int r = 0; r < RM; ++r) chosen += (r < R && dbits(S[r]) <= tb) ? 1 : 0;
+                        if (chosen >= R) {                     // rounding guard
+                            chosen = 0;
 #pragma unroll
-                        for (int r = 0; r < RM; ++r)
-                            if (r < R && dbits(a[r]) != 0) chosen = r;
+                            for (int r = 0; r < RM; ++r)
+                                if (r < R && dbits(a[r]) != 0) chosen = r;
+                        }
                     }
                     const int nch = sh.net.n_change[chosen];
                     for (int i = 0; i < nch; ++i) {
@@ -283,7 +320,9 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                     }
                     t = t_next;
                     ++fired;
-                    mask = sh.net.dep[chosen];
+                    // the next trip's recompute: a mask of reactions, or (dependency
+                    // lists) the fired reaction itself
+                    mask = kDepList ? static_cast<uint32_t>(chosen) : sh.net.dep[chosen];
                     done = false;
                 }
             }

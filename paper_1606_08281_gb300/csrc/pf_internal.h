@@ -20,6 +20,8 @@ struct NetTables {
     int8_t ch_sp[PF_MAX_REACTIONS][PF_MAX_SPECIES];
     int16_t ch_delta[PF_MAX_REACTIONS][PF_MAX_SPECIES];
     uint32_t dep[PF_MAX_REACTIONS];
+    int8_t n_dep[PF_MAX_REACTIONS];                      // popcount of dep[r]
+    int8_t dep_list[PF_MAX_REACTIONS][PF_MAX_REACTIONS]; // the reactions of dep[r], ascending
     int32_t x0[PF_MAX_SPECIES];
     double C[PF_MAX_OBS_DIM][PF_MAX_SPECIES];
     double sigma[PF_MAX_OBS_DIM];
