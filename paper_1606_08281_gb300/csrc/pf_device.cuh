@@ -240,6 +240,24 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                         a[r] = propensity<UM>(r, sh, L);
                     }
                 }
+            } else if (kHoist && mask != all) {
+                // small networks: the fired reaction's dependents one by one,
+                // written into the register array through select chains
+                const int c = static_cast<int>(mask);
+                const int nd = sh.net.n_dep[c];
+                for (int i = 0; i < nd; ++i) {
+                    const int r = sh.net.dep_list[c][i];
+                    double rate = rate_reg[0];
+                    int desc = desc_reg[0];
+#pragma unroll
+                    for (int q = 1; q < (kHoist ? RM : 1); ++q) {
+                        rate = r == q ? rate_reg[q] : rate;
+                        desc = r == q ? desc_reg[q] : desc;
+                    }
+                    const double v = (desc & 0xFF) == 0 ? rate : propensity_reg<UM>(rate, desc, L);
+#pragma unroll
+                    for (int q = 0; q < RM; ++q) a[q] = r == q ? v : a[q];
+                }
             } else {
 #pragma unroll
                 for (int r = 0; r < RM; ++r) {
@@ -322,7 +340,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                     ++fired;
                     // the next trip's recompute: a mask of reactions, or (dependency
                     // lists) the fired reaction itself
-                    mask = kDepList ? static_cast<uint32_t>(chosen) : sh.net.dep[chosen];
+                    mask = (kDepList || kHoist) ? static_cast<uint32_t>(chosen) : sh.net.dep[chosen];
                     done = false;
                 }
             }
