@@ -25,11 +25,14 @@
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter = (draw j, particle i, (trajectory << 20) | interval k, theta m);
  *     the resampling uniform of interval k uses particle lane 0xFFFFFFFF;
- *   - uniforms: u1 = ((w1:w0 >> 11) + 1) 2^-53 in (0,1],
- *               u2 = (w3:w2 >> 11) 2^-53 in [0,1);
+ *   - the waiting time's exponential variate E (tau = E / a0) comes from the
+ *     ziggurat method of Marsaglia & Tsang ("The ziggurat method for
+ *     generating random variables", J. Stat. Softw. 5(8), 2000) with 256
+ *     layers and their published r and v; see exp_variate() for the words it
+ *     consumes; u2 = (w3:w2 >> 11) 2^-53 in [0,1) selects the reaction;
  *   - propensity a_r = theta[rho(r)] * prod_u binom(x_u, p_ru)  (Gillespie's
  *     combinatorial mass action), prefix sums in reaction order;
- *   - tau = -log(u1)/a0; a draw whose time passes the observation time is
+ *   - tau = E/a0; a draw whose time passes the observation time is
  *     discarded (memorylessness) and the next interval draws afresh;
  *   - Gaussian measurement density N(y; C x, diag sigma^2) with its full
  *     normalising constant;
@@ -81,6 +84,88 @@ static void draw4(uint64_t seed, uint32_t j, uint32_t i, uint32_t lane, uint32_t
     uint32_t ctr[4] = {j, i, lane, m};
     uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
     orc_philox4x32_10(ctr, key, w);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Exponential variates by the ziggurat method (Marsaglia & Tsang 2000).      */
+/* Layers i = 0..255 of equal area v under f(x) = exp(-x): x_1 = r,           */
+/* x_{i+1} = -log(v / x_i + f(x_i)), x_256 = 0, and the base layer's virtual  */
+/* width x_0 = v / f(r) (base strip [0, r] plus the tail beyond r).            */
+/* ------------------------------------------------------------------------ */
+#define ZIG_N 256
+static const double zig_r = 7.69711747013104972;
+static const double zig_v = 0.0039496598225815571993;
+static double zig_x[ZIG_N + 1], zig_f[ZIG_N + 1];
+static int zig_ready = 0;
+
+static void zig_init(void) {
+    if (zig_ready) return;
+    zig_x[0] = zig_v / exp(-zig_r);
+    zig_x[1] = zig_r;
+    for (int i = 1; i < ZIG_N - 1; i++) zig_x[i + 1] = -log(zig_v / zig_x[i] + exp(-zig_x[i]));
+    zig_x[ZIG_N] = 0.0;
+    for (int i = 0; i <= ZIG_N; i++) zig_f[i] = exp(-zig_x[i]);
+    zig_ready = 1;
+}
+
+/* The 64-bit words a draw may consume, in order: word 0 = w1:w0 of the draw's
+ * Philox block (counter j, particle, lane, m); then, for s = 1, 2, ...,
+ * w1:w0 and w3:w2 of the block with counter (j, particle | s << 16, lane, m). */
+typedef struct {
+    uint64_t seed;
+    uint32_t j, particle, lane, m;
+    uint32_t s;
+    uint32_t w[4];
+    int have;
+} word_stream;
+
+static uint64_t next_word(word_stream *ws) {
+    if (ws->have == 0) {
+        ws->s++;
+        draw4(ws->seed, ws->j, ws->particle | (ws->s << 16), ws->lane, ws->m, ws->w);
+        ws->have = 2;
+        return ((uint64_t)ws->w[1] << 32) | ws->w[0];
+    }
+    ws->have = 0;
+    return ((uint64_t)ws->w[3] << 32) | ws->w[2];
+}
+
+/* E ~ Exp(1).  Each attempt takes one word: layer i = its low 8 bits,
+ * u = (word >> 11) 2^-53, x = u x_i.  Accept x if x < x_{i+1}; else the base
+ * layer returns r plus an Exp(1) tail variate -log(u'), u' = ((w >> 11) + 1)
+ * 2^-53 from the next word; other layers accept x if
+ * f_i + U (f_{i+1} - f_i) < exp(-x), U = (w >> 11) 2^-53 from the next word,
+ * and otherwise start a new attempt with the next word. */
+static double exp_variate(uint64_t first_word, word_stream *ws) {
+    uint64_t W = first_word;
+    for (;;) {
+        int i = (int)(W & 0xFF);
+        double u = (double)(W >> 11) * 0x1p-53;
+        double x = u * zig_x[i];
+        if (x < zig_x[i + 1]) return x;
+        if (i == 0) {
+            uint64_t W2 = next_word(ws);
+            double u1 = (double)((W2 >> 11) + 1) * 0x1p-53;
+            return zig_r + -log(u1);
+        }
+        uint64_t W2 = next_word(ws);
+        double U = (double)(W2 >> 11) * 0x1p-53;
+        double y = zig_f[i] + U * (zig_f[i + 1] - zig_f[i]);
+        if (y < exp(-x)) return x;
+        W = next_word(ws);
+    }
+}
+
+/* n exponential variates from the stream of draw counter j = 0..n-1 of
+ * particle 0, lane 0, theta 0 (for testing the generator's law). */
+void orc_exp_variates(uint64_t seed, int64_t n, double *out) {
+    zig_init();
+    for (int64_t k = 0; k < n; k++) {
+        uint32_t w[4];
+        draw4(seed, (uint32_t)k, 0u, 0u, 0u, w);
+        word_stream ws = {seed, (uint32_t)k, 0u, 0u, 0u, 0u, {0, 0, 0, 0}, 0};
+        out[k] = exp_variate(((uint64_t)w[1] << 32) | w[0], &ws);
+    }
 }
 
 /* ------------------------------------------------------------------------ */
@@ -138,9 +223,10 @@ static int ssa_advance(const orc_net *net, const double *theta, int64_t *x, doub
         j++;
         uint64_t r0 = ((uint64_t)w[1] << 32) | w[0];
         uint64_t r1 = ((uint64_t)w[3] << 32) | w[2];
-        double u1 = (double)((r0 >> 11) + 1) * 0x1p-53;
+        word_stream ws = {seed, (uint32_t)(j - 1), particle, lane, m, 0u, {0, 0, 0, 0}, 0};
+        double E = exp_variate(r0, &ws);
         double u2 = (double)(r1 >> 11) * 0x1p-53;
-        double tau = -log(u1) / a0;
+        double tau = E / a0;
         double t_next = t + tau;
         if (t_next > t_end) return ORC_OK; /* the pending event lies beyond t_end */
         double target = u2 * a0;
@@ -328,6 +414,7 @@ int orc_pf_loglik(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
                   double *ll_traj, uint64_t *events, uint64_t *digest, int32_t *final_states) {
     orc_net net = {U, R, reac, prod, rate_index};
     if (check_network(&net, d)) return ORC_EINVAL;
+    zig_init();
     if (N < 1 || N > 16384 || K < 1 || T < 1 || P < 1 || T >= 4096 || K >= (1 << 20))
         return ORC_EINVAL;
     for (int64_t mi = 0; mi < M; mi++) {
@@ -365,6 +452,7 @@ int orc_ssa_paths(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
                   int32_t *states_out, uint64_t *fired_out, uint8_t *status_out) {
     orc_net net = {U, R, reac, prod, rate_index};
     if (check_network(&net, d)) return ORC_EINVAL;
+    zig_init();
     double *a = (double *)malloc(sizeof(double) * (size_t)R);
     double *S = (double *)malloc(sizeof(double) * (size_t)R);
     int64_t *x = (int64_t *)malloc(sizeof(int64_t) * (size_t)U);

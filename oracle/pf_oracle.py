@@ -48,6 +48,8 @@ def _bind(path: Path) -> ct.CDLL:
     lib.orc_ssa_paths.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, ct.c_int32, P, P,
                                   ct.c_int32, ct.c_int64, ct.c_uint64, ct.c_uint64, P, P, P]
     lib.orc_ssa_paths.restype = ct.c_int
+    lib.orc_exp_variates.argtypes = [ct.c_uint64, ct.c_int64, P]
+    lib.orc_exp_variates.restype = None
     return lib
 
 
@@ -99,6 +101,12 @@ class Oracle:
         lib.orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
         return out
 
+
+    def exp_variates(self, seed: int, n: int) -> np.ndarray:
+        """n Exp(1) variates of the ziggurat generator (draw counters 0..n-1)."""
+        out = np.empty(n, np.float64)
+        self._lib.orc_exp_variates(ct.c_uint64(int(seed)), int(n), _ptr(out))
+        return out
 
     def resample_systematic(self, q, r64: int) -> np.ndarray:
         """Ancestor indices of integer-weight systematic resampling."""
@@ -196,6 +204,10 @@ def philox4x32_10(ctr, key):
 
 def resample_systematic(q, r64: int):
     return default().resample_systematic(q, r64)
+
+
+def exp_variates(seed: int, n: int):
+    return default().exp_variates(seed, n)
 
 
 def pf_loglik(*args, **kwargs):

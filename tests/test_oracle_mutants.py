@@ -16,8 +16,10 @@ MUTANTS = {
     "transpose_C": ("mu = mu + Cm[p * U + u] *", "mu = mu + Cm[u * P + p] *", "single_particle"),
     "power_law_propensity": ("return x * (x - 1) / 2; /* p == 2 */", "return x * x;",
                              "second_order"),
-    "time_times_a0": ("double tau = -log(u1) / a0;", "double tau = -log(u1) * a0;",
-                      "birth_death_law"),
+    "time_times_a0": ("double tau = E / a0;", "double tau = E * a0;", "birth_death_law"),
+    "ziggurat_no_wedge_test": ("if (y < exp(-x)) return x;", "return x;", "exp_law"),
+    "ziggurat_tail_without_offset": ("return zig_r + -log(u1);", "return -log(u1);", "exp_law"),
+    "ziggurat_layer_bits": ("int i = (int)(W & 0xFF);", "int i = (int)(W & 0x7F);", "exp_law"),
     "stoichiometry_sign": ("x[u] += net->prod[chosen * net->U + u] - net->reac[chosen * net->U + u];",
                            "x[u] += net->reac[chosen * net->U + u] - net->prod[chosen * net->U + u];",
                            "birth_death_law"),
@@ -41,6 +43,7 @@ CHECKS = {
     "resampling": lambda o, kat: pins.check_resampling(o),
     "philox": lambda o, kat: pins.check_philox(o, kat),
     "unbiased": lambda o, kat: pins.check_unbiased(o, S=150, N=100),
+    "exp_law": lambda o, kat: pins.check_exp_variates(o),
 }
 
 

@@ -42,6 +42,32 @@ def test_philox_known_answers(kat_vectors):
     check_philox(orc(), kat_vectors)
 
 
+# ------------------------------------------------- exponential variates ---
+def check_exp_variates(o, n=400_000):
+    """The ziggurat generator's law is Exp(1): Kolmogorov-Smirnov against the
+    exponential CDF, mean and variance 1, and the tail beyond the ziggurat's
+    base x = r = 7.697 (handled by a separate branch) has mass exp(-r)."""
+    e = o.exp_variates(2024, n)
+    assert (e >= 0).all()
+    assert stats.kstest(e, "expon").pvalue > 1e-3
+    assert abs(e.mean() - 1.0) < 5 / np.sqrt(n)
+    assert abs(e.var() - 1.0) < 5 * np.sqrt(8.0 / n)
+    r = 7.69711747013104972
+    big = o.exp_variates(77, 4_000_000)
+    k = int((big > r).sum())
+    lam = 4_000_000 * np.exp(-r)
+    assert abs(k - lam) < 5 * np.sqrt(lam)
+    # just below the base strip and inside the wedges the density is exp(-x) too
+    for a, b in [(0.0, 0.01), (2.0, 2.5), (5.0, 7.6)]:
+        want = np.exp(-a) - np.exp(-b)
+        got = np.mean((big >= a) & (big < b))
+        assert abs(got - want) < 5 * np.sqrt(want / 4_000_000)
+
+
+def test_exponential_variates_law():
+    check_exp_variates(orc())
+
+
 # ------------------------------------------------------- exact likelihood ---
 @pytest.mark.parametrize("k1,k2,dt", [(10.0, 0.2, 1.0), (30.0, 0.9, 0.5), (3.0, 0.05, 2.0)])
 def test_exact_transition_two_routes(k1, k2, dt):
