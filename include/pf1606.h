@@ -345,6 +345,16 @@ int pf_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters,
  */
 int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n);
 
+/*
+ * pf_exp_variates -- the device's Exp(1) generator of the SSA waiting time
+ * (tau = E / a0; Gillespie's direct method, Sec. "The stochastic birth-death
+ * Model"), exposed for tests: out[k] = the variate of draw counter k of
+ * particle 0, interval word 0, theta row 0 under key `seed`.  Ziggurat method
+ * (Marsaglia & Tsang, J. Stat. Softw. 5(8), 2000), 256 layers.  Host output;
+ * synchronous.  Returns PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.
+ */
+int pf_exp_variates(uint64_t seed, int64_t n, double *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -14,6 +14,7 @@
 
 #include "pf1606.h"
 #include "pf_internal.h"
+#include "ziggurat.cuh"
 
 namespace {
 thread_local std::string g_last_error;
@@ -195,6 +196,11 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     if (rc) return rc;
     rc = check_count_range(a.net, K, budget);
     if (rc) return rc;
+    {
+        int ze = 0;
+        a.zig = pf::zig_table_device(&ze);
+        if (!a.zig) return cuda_fail(ze, "ziggurat table");
+    }
     int B = o.block_threads;
     if (B == 0) B = std::min(128, ((N + 31) / 32) * 32);
     if (B < 32 || B > 128 || (B % 32)) return fail(PF_EINVAL, "block_threads %d must be a multiple of 32 in 32..128", B);
@@ -390,6 +396,11 @@ extern "C" int pf_loglik_noalloc(const pf_network *net, const double *thetas, in
     if (rc) return rc;
     rc = check_count_range(a.net, K, budget);
     if (rc) return rc;
+    {
+        int ze = 0;
+        a.zig = pf::zig_table_device(&ze);
+        if (!a.zig) return cuda_fail(ze, "ziggurat table");
+    }
     const int B = std::min(128, ((N + 31) / 32) * 32);
     const size_t smem = pf::filter_smem_bytes(N, a.net.U, false);
     int dev = 0, smem_max = 0;

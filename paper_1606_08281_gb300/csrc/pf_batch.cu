@@ -93,7 +93,7 @@ template <int RM, int UM, bool GLOBAL>
 __global__ void __launch_bounds__(kBlock, 4)
 batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *items, int group,
              unsigned long long *counters, unsigned char *slab, size_t slab_bytes, double *ll_f,
-             uint8_t *st_f, unsigned long long *ev_f) {
+             uint8_t *st_f, unsigned long long *ev_f, const ZigTab *zig) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SharedHead sh;
     __shared__ RequestDev rq;
@@ -101,6 +101,7 @@ batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *ite
     __shared__ uint64_t item;
     __shared__ const ProblemDev *loaded;
     load_log_table(sh.logt);
+    load_zig_table(sh.zig, zig);
     if (threadIdx.x == 0) loaded = nullptr;
     const long long begin = hdr->group_begin[group];
     const unsigned long long count = static_cast<unsigned long long>(hdr->group_count[group]);
@@ -184,7 +185,7 @@ __global__ void batch_reduce_kernel(const BatchHeader *hdr, const RequestDev *re
 // ---------------------------------------------------------------- groups
 using BatchKernel = void (*)(const BatchHeader *, const RequestDev *, const uint64_t *, int,
                              unsigned long long *, unsigned char *, size_t, double *, uint8_t *,
-                             unsigned long long *);
+                             unsigned long long *, const ZigTab *);
 
 BatchKernel group_kernel(int g) {
     switch (g) {
@@ -367,6 +368,9 @@ int init_slot(pf_ctx *ctx, int si) {
         CTX_CUDA(cudaStreamCreateWithFlags(&s.side[g], cudaStreamNonBlocking), "stream");
         CTX_CUDA(cudaEventCreateWithFlags(&s.join[g], cudaEventDisableTiming), "event");
     }
+    int ze = 0;
+    const ZigTab *zig = zig_table_device(&ze);
+    if (!zig) return pf::cuda_fail(ze, "ziggurat table");
     // capture: reset -> persistent group kernels (forked) -> reduce
     CTX_CUDA(cudaStreamBeginCapture(s.stream, cudaStreamCaptureModeThreadLocal), "capture");
     reset_kernel<<<1, 32, 0, s.stream>>>(s.counters);
@@ -376,7 +380,7 @@ int init_slot(pf_ctx *ctx, int si) {
         cudaStreamWaitEvent(s.side[g], s.fork, 0);
         group_kernel(g)<<<s.grid[g], kBlock, s.smem[g], s.side[g]>>>(
             s.hdr_d, s.req_d, s.items_d, g, s.counters, s.slab[g], ctx->slab_bytes, s.ll_f, s.st_f,
-            s.ev_f);
+            s.ev_f, zig);
         cudaEventRecord(s.join[g], s.side[g]);
         cudaStreamWaitEvent(s.stream, s.join[g], 0);
     }

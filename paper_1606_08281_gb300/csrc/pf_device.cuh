@@ -31,6 +31,7 @@
 #include "fastmath.cuh"
 #include "pf_internal.h"
 #include "philox.cuh"
+#include "ziggurat.cuh"
 
 namespace pf {
 namespace dev {
@@ -61,6 +62,7 @@ struct SharedHead {
     int bucket[16];
     float rate_f[PF_MAX_REACTIONS];  // FP32 copy of rate[], for cost estimates only
     LogTab logt;
+    ZigTab zig;
 };
 
 // ------------------------------------------------------------------ helpers
@@ -296,11 +298,13 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
             } else {
                 const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow,
                                                 key0, key1);
-                ++draws;
                 const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
                 const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
-                // tau = -log(u1) / a0 with u1 = ((r0 >> 11) + 1) 2^-53 in (0, 1]
-                const double tau = __ddiv_rn(neg_log_u53((r0 >> 11) + 1ull, sh.logt), a0);
+                // tau = E / a0 with E ~ Exp(1) from the ziggurat
+                const double E = zig_exp(r0, draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
+                                         key1, sh.zig, sh.logt);
+                ++draws;
+                const double tau = __ddiv_rn(E, a0);
                 const double t_next = __dadd_rn(t, tau);
                 if (dbits(t_next) > t_end_bits) {
                     done = true;                               // the event lies past t_end

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "pf_device.cuh"
 
@@ -52,6 +53,7 @@ __global__ void __launch_bounds__(128, 4) filter_kernel(const FilterArgs args) {
         for (int i = tid; i < static_cast<int>(sizeof(NetTables) / 4); i += B) dst[i] = src[i];
     }
     load_log_table(sh.logt);
+    load_zig_table(sh.zig, args.zig);
     __syncthreads();
     FilterJob job;
     job.theta = args.thetas + mrow * args.net.d;
@@ -91,6 +93,7 @@ __global__ void __launch_bounds__(128, 4) filter_kernel_global(const FilterArgs 
         for (int i = tid; i < static_cast<int>(sizeof(NetTables) / 4); i += B) dst[i] = src[i];
     }
     load_log_table(sh.logt);
+    load_zig_table(sh.zig, args.zig);
     unsigned char *arrays = slabs + static_cast<size_t>(blockIdx.x) * slab_bytes;
     const int64_t F = args.M * T;
     for (int64_t slot = blockIdx.x; slot < F; slot += gridDim.x) {
@@ -335,6 +338,46 @@ int launch_schedule(const FilterArgs &a, uint32_t *cost, uint32_t *order, uint32
     if (e != cudaSuccess) return e;
     order_kernel<<<1, 1024, 0, s>>>(cost, a.M, order);
     return cudaGetLastError();
+}
+
+static __device__ ZigTab g_zig_table;
+
+// The ziggurat table, written from its recurrence with the host C library's
+// exp and log (x_1 = r, x_{i+1} = -log(v / x_i + exp(-x_i)), x_256 = 0,
+// x_0 = v / exp(-r), f_i = exp(-x_i)).
+static void build_zig_table(ZigTab &t) {
+    t.x[0] = kZigV / std::exp(-kZigR);
+    t.x[1] = kZigR;
+    for (int i = 1; i < kZigLayers - 1; ++i) t.x[i + 1] = -std::log(kZigV / t.x[i] + std::exp(-t.x[i]));
+    t.x[kZigLayers] = 0.0;
+    for (int i = 0; i <= kZigLayers; ++i) t.f[i] = std::exp(-t.x[i]);
+}
+
+const ZigTab *zig_table_device(int *err) {
+    static std::mutex mu;
+    static const ZigTab *addr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess && (dev < 0 || dev >= 64)) e = cudaErrorInvalidDevice;
+    if (e != cudaSuccess) {
+        *err = e;
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        ZigTab host;
+        build_zig_table(host);
+        void *p = nullptr;
+        e = cudaMemcpyToSymbol(g_zig_table, &host, sizeof(ZigTab));
+        if (e == cudaSuccess) e = cudaGetSymbolAddress(&p, g_zig_table);
+        if (e != cudaSuccess) {
+            *err = e;
+            return nullptr;
+        }
+        addr[dev] = static_cast<const ZigTab *>(p);
+    }
+    *err = cudaSuccess;
+    return addr[dev];
 }
 
 int launch_fill(double *p, int64_t n, double value, void *stream) {

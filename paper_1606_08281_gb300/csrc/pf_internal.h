@@ -6,6 +6,8 @@
 
 namespace pf {
 
+struct ZigTab;
+
 // Network tables in the form the kernels use.  Reactant side: at most two
 // (species, order) pairs because the total order is <= 2 (sp = -1: none).
 // Change side: a compact list of (species, delta) per reaction.  dep[r] has
@@ -47,6 +49,7 @@ struct FilterArgs {
     double *acc;                // [M] running upper bounds for early rejection (null: off)
     double reject_below;
     double slack;               // upper bound of one per-time-point log increment, >= 0
+    const ZigTab *zig;          // device copy of the exponential ziggurat table
 };
 
 // Bytes of the particle population of one filter: N (8 + 4U + 4) bytes, plus

@@ -11,6 +11,7 @@
 
 #include "fastmath.cuh"
 #include "pf1606.h"
+#include "ziggurat.cuh"
 
 namespace {
 
@@ -119,5 +120,35 @@ extern "C" int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n) {
     }
     cudaFree(dv);
     cudaFree(dout);
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+namespace {
+__global__ void exp_variates_kernel(uint64_t seed, int64_t n, const pf::ZigTab *zig, double *out) {
+    __shared__ pf::LogTab lt;
+    __shared__ pf::ZigTab zt;
+    pf::load_log_table(lt);
+    pf::load_zig_table(zt, zig);
+    __syncthreads();
+    const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    const pf::Philox4 w = pf::philox4x32_10(static_cast<uint32_t>(k), 0u, 0u, 0u, k0, k1);
+    const uint64_t first = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+    out[k] = pf::zig_exp(first, static_cast<uint32_t>(k), 0u, 0u, 0u, k0, k1, zt, lt);
+}
+}  // namespace
+
+extern "C" int pf_exp_variates(uint64_t seed, int64_t n, double *out) {
+    if (n < 0 || n > 0xFFFFFFFFll || (n > 0 && !out)) return PF_EINVAL;
+    if (n == 0) return PF_OK;
+    int ze = 0;
+    const pf::ZigTab *zig = pf::zig_table_device(&ze);
+    if (!zig) return PF_ECUDA;
+    double *d = nullptr;
+    if (cudaMalloc(&d, n * sizeof(double)) != cudaSuccess) return PF_ENOMEM;
+    exp_variates_kernel<<<static_cast<unsigned>((n + 255) / 256), 256>>>(seed, n, zig, d);
+    cudaError_t e = cudaMemcpy(out, d, n * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(d);
     return e == cudaSuccess ? PF_OK : PF_ECUDA;
 }
