@@ -409,7 +409,8 @@ def fp64_probe(pf) -> dict:
     res = {}
     iters = {0: 4096, 1: 256, 2: 512}
     iters[3] = 512
-    for kind in (0, 1, 2, 3):
+    iters[4] = 512
+    for kind in (0, 1, 2, 3, 4):
         pf.pf_fp64_probe(kind, blocks, threads, 16)          # warm-up
         ms, _ = pf.pf_fp64_probe(kind, blocks, threads, iters[kind])
         res[kind] = ms
@@ -418,7 +419,10 @@ def fp64_probe(pf) -> dict:
     log_rate = ops * iters[1] / (res[1] * 1e-3)            # log calls (+2 adds) per second
     div_rate = ops * iters[2] / (res[2] * 1e-3)
     mylog_rate = ops * iters[3] / (res[3] * 1e-3)
+    exp_rate = ops * iters[4] / (res[4] * 1e-3)
     return {
+        "exp_per_s": exp_rate,
+        "exp_fma_equiv_flops": 2 * fma_rate / exp_rate - 2.0,
         "table_log_per_s": mylog_rate,
         "fma_tflops": 2 * fma_rate / 1e12,
         "log_per_s": log_rate, "div_per_s": div_rate,

@@ -326,7 +326,8 @@ int pf_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, in
  *   kind 1: log() plus two additions per chain step;
  *   kind 2: IEEE division plus two additions per chain step;
  *   kind 3: the library's table-driven -log(u) (pf_neg_log_u53) plus one
- *           addition per chain step.
+ *           addition per chain step;
+ *   kind 4: exp() plus two additions per chain step.
  * With ncu's FP64 instruction counters this prices one log() and one division
  * in FP64 operations, the per-event cost model of the SSA kernel's roofline.
  * Returns PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.  Allocates and frees its

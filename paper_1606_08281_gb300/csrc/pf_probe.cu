@@ -38,6 +38,13 @@ __global__ void probe_kernel(int kind, int64_t iters, double *out) {
                 acc[c] = __dadd_rn(acc[c], log(x[c]));
                 x[c] = __dadd_rn(x[c], 1e-12);
             }
+    } else if (kind == 4) {
+        for (int64_t i = 0; i < iters; ++i)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) {
+                acc[c] = __dadd_rn(acc[c], exp(-x[c]));
+                x[c] = __dadd_rn(x[c], 1e-12);
+            }
     } else if (kind == 2) {
         for (int64_t i = 0; i < iters; ++i)
 #pragma unroll
@@ -67,7 +74,7 @@ __global__ void probe_kernel(int kind, int64_t iters, double *out) {
 
 extern "C" int pf_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters,
                              double *elapsed_ms, double *checksum) {
-    if (kind < 0 || kind > 3 || blocks < 1 || threads < 32 || threads > 1024 || iters < 1 ||
+    if (kind < 0 || kind > 4 || blocks < 1 || threads < 32 || threads > 1024 || iters < 1 ||
         !elapsed_ms)
         return PF_EINVAL;
     double *d = nullptr;
