@@ -207,9 +207,11 @@ int tier_of(const NetTables &t) {
     return 3;
 }
 
-// Shared-memory population arena of the on-chip groups (bytes): tier 0 is
-// sized so that four blocks fit an SM (gene-expression sized filters).
-size_t shared_arena(int tier) { return tier == 0 ? 40u << 10 : 48u << 10; }
+// Shared-memory population arena of the on-chip groups (bytes), next to the
+// ~32 KB of per-block tables: tier 0 fits four blocks per SM (up to ~1200
+// particles of 2 species), the larger tiers three (e.g. 700 particles of 10
+// species).
+size_t shared_arena(int tier) { return tier == 0 ? 24u << 10 : 36u << 10; }
 
 size_t population_bytes(int N, int U) { return filter_smem_bytes(N, U, false); }
 
