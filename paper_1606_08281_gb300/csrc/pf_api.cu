@@ -210,7 +210,7 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     PF_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
     PF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     // populations that do not fit on chip (with the block's static tables) go to global memory
-    const bool on_chip = smem + 16384 <= (size_t)smem_max;
+    const bool on_chip = smem + pf::filter_static_smem() <= (size_t)smem_max;
 
     cudaStream_t s = static_cast<cudaStream_t>(o.stream);
     // observation times (always a host array): strictly increasing, >= 0, finite
@@ -406,7 +406,7 @@ extern "C" int pf_loglik_noalloc(const pf_network *net, const double *thetas, in
     int dev = 0, smem_max = 0;
     PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     PF_CUDA(cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "cudaDeviceGetAttribute");
-    if (smem + sizeof(pf::NetTables) + 8192 > (size_t)smem_max)
+    if (smem + pf::filter_static_smem() > (size_t)smem_max)
         return fail(PF_EINVAL, "N=%d with U=%d needs %zu bytes of shared memory per filter (limit %d)", N, a.net.U, smem, smem_max);
     for (int k = 0; k < K; ++k) {
         const bool bad = !std::isfinite(obs_times[k]) ||

@@ -294,6 +294,8 @@ int reaction_tier(int R) {
 
 int global_grid(int sms) { return sms * 2; }
 
+size_t filter_static_smem() { return sizeof(SharedHead) + 2048; }
+
 int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, void *stream,
                   unsigned char *slabs, size_t slab_bytes, int grid) {
     if (a.M == 0) return cudaSuccess;

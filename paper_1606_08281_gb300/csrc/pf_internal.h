@@ -70,6 +70,10 @@ int launch_filter(const FilterArgs &a, int block_threads, double *loglik, uint8_
 // Resident blocks for the global-memory variant on a GPU with `sms` SMs.
 int global_grid(int sms);
 
+// Static shared memory of a filter block (its tables) plus a safety margin:
+// a population fits on chip when population + this <= the opt-in maximum.
+size_t filter_static_smem();
+
 // p[0..n) = value on `stream`.
 int launch_fill(double *p, int64_t n, double value, void *stream);
 

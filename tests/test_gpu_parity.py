@@ -117,6 +117,12 @@ def test_global_memory_populations(pf):
     g, o = run_both(pf, w.net, w.thetas(3), w.x0, w.obs_times, w.observations(), w.C, w.sigma,
                     16384, 22)
     assert_parity(g, o)
+    # just below and just above the shared-memory limit (population + tables)
+    w = W.gene_expression().subset(T=1, K=3)
+    for N in (8000, 9200, 9800):
+        g, o = run_both(pf, w.net, w.thetas(1), w.x0, w.obs_times, w.observations(), w.C,
+                        w.sigma, N, 23)
+        assert_parity(g, o)
 
 
 def test_observation_at_time_zero_and_single_time(pf):
