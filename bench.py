@@ -42,13 +42,22 @@ FP64_FLOPS_PER_SM_CLK = 4.0
 N_SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = FP64_FLOPS_PER_SM_CLK * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
-# FP64 flops (FMA = 2) of the two transcendental steps of an SSA event, as the
-# library computes them, counted by ncu's FP64 instruction counters on the
-# pf_fp64_probe kernels: the table-driven -log(u) is 4 DADD + 2 DMUL +
-# 6 DFMA (= 18 flops, 12 operations); the IEEE division is 7 DFMA + 1 DMUL
-# (= 15 flops, 8 operations).
-FP64_FLOPS_LOG, FP64_OPS_LOG = 18.0, 12.0
-FP64_FLOPS_DIV, FP64_OPS_DIV = 15.0, 8.0
+# FP64 cost of the SSA event's variate and division, counted by ncu's FP64
+# instruction counters on the pf_fp64_probe kernels (FMA = 2 flops):
+#   IEEE division: 7 DFMA + 1 DMUL = 8 operations, 15 flops;
+#   exp(): 14 DFMA + 2 DADD = 16 operations, 30 flops;
+#   the table-driven -log(u): 6 DFMA + 2 DMUL + 4 DADD = 12 operations, 18 flops.
+# The Exp(1) variate is a 1024-layer ziggurat: one multiply when the fast path
+# accepts; with probability P_WEDGE a wedge test (3 operations + exp), with
+# probability P_TAIL the tail (log + 1 add).  P_WEDGE + P_TAIL = 1 - mean of
+# x_{i+1}/x_i over the layers = 0.006423; P_TAIL = (1/1024) / (r + 1).
+FP64_OPS_DIV, FP64_FLOPS_DIV = 8.0, 15.0
+FP64_OPS_EXP, FP64_FLOPS_EXP = 16.0, 30.0
+FP64_OPS_LOG, FP64_FLOPS_LOG = 12.0, 18.0
+P_TAIL = (1.0 / 1024) / (9.2561645442655436867 + 1.0)
+P_WEDGE = 0.006423 - P_TAIL
+ZIG_OPS = 1.0 + P_WEDGE * (3.0 + FP64_OPS_EXP) + P_TAIL * (1.0 + FP64_OPS_LOG)
+ZIG_FLOPS = 1.0 + P_WEDGE * (3.0 + FP64_FLOPS_EXP) + P_TAIL * (1.0 + FP64_FLOPS_LOG)
 
 
 # DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression
@@ -59,13 +68,14 @@ FILTER_TRAFFIC_BYTES = 19.1e6
 
 def flops_per_event(R: int) -> float:
     """Algorithmic FP64 flops of one direct-method SSA event: R propensity
-    products, R-1 prefix additions, u2*a0, t + tau, one log, one division."""
-    return R + (R - 1) + 1.0 + 1.0 + FP64_FLOPS_LOG + FP64_FLOPS_DIV
+    products, R-1 prefix additions, u2*a0, t + tau, one Exp(1) variate
+    (ziggurat, expected cost), one division."""
+    return R + (R - 1) + 1.0 + 1.0 + ZIG_FLOPS + FP64_FLOPS_DIV
 
 
 def ops_per_event(R: int) -> float:
     """The same work in FP64 pipe operations (each DFMA/DMUL/DADD = 1)."""
-    return R + (R - 1) + 1.0 + 1.0 + FP64_OPS_LOG + FP64_OPS_DIV
+    return R + (R - 1) + 1.0 + 1.0 + ZIG_OPS + FP64_OPS_DIV
 
 
 # ---------------------------------------------------------------- clocks
@@ -232,6 +242,7 @@ def main() -> None:
                          "heterogeneous request mix vs plain per-request launches; serve: a "
                          "Poisson request stream, continuous batching vs a plain FIFO server")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--autotune", action="store_true",
                     help="tune block size and launch order on a theta sample before timing")
     a = ap.parse_args()
@@ -361,7 +372,7 @@ def main() -> None:
             "gpu_launches": 2 * a.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": FILTER_TRAFFIC_BYTES if w.name == WORKLOAD and w.M == 4096 else None,
+                         "traffic": None,
                          "kernel": "filter_kernel (FP64 pipe)",
                          "flops_per_event": fpe,
                          "fp64_ops_per_event": ops_per_event(w.R),
@@ -392,12 +403,12 @@ def run_pattern(a) -> None:
                                        "N 256-4096, K 10-100 (seed 4001)"},
                 "plain_per_request": res["plain_theta_per_s"], **res}
     else:
-        stream = W.serving_stream(duration_s=a.serve_seconds)
+        stream = W.serving_stream(rate_hz=a.serve_rate, duration_s=a.serve_seconds)
         res = serving.run_serving(stream)
         line = {"metric": "theta-likelihoods/s", "mode": "serving",
                 "value": res["batched"]["theta_per_s"], "unit": "theta-likelihoods/s",
                 "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"Poisson 200/s for {a.serve_seconds:.0f} s (seed 5001): "
+                "config": {"workload": f"Poisson {a.serve_rate:.0f}/s for {a.serve_seconds:.0f} s (seed 5001): "
                                        "gene_expression (theta 4-512, N 256, K 10) and cascade "
                                        "(theta 1-32, N 128, K 5), coin-flipped"},
                 **res}
