@@ -64,8 +64,21 @@ __device__ __forceinline__ double zig_exp(uint64_t first, uint32_t j, uint32_t p
         if (i == 0) return __dadd_rn(kZigR, neg_log_u53((W2 >> 11) + 1ull, lt));
         const uint64_t v2 = W2 >> 11;
         const double U = v2 ? scaled_u53(v2) : 0.0;
-        const double y = __dadd_rn(z.f[i], __dmul_rn(U, __dsub_rn(z.f[i + 1], z.f[i])));
-        if (y < exp(-x)) return x;
+        const double df = __dsub_rn(z.f[i + 1], z.f[i]);
+        const double y = __dadd_rn(z.f[i], __dmul_rn(U, df));
+        // Squeeze (decides like y < exp(-x) without exp): on [x_{i+1}, x_i] the
+        // convex exp(-x) lies above its tangent at x_i, f_i (1 + (x_i - x)), and
+        // below the chord; a relative margin of 1e-12 keeps both tests exact
+        // against any rounding of y and exp.
+        const double d = __dsub_rn(z.x[i], x);
+        const double tangent = __dmul_rn(z.f[i], __dadd_rn(1.0, d));
+        if (y < __dmul_rn(tangent, 1.0 - 1e-12)) return x;
+        // above the chord: (y - f_i) / df = U > d / (x_i - x_{i+1})
+        if (__dmul_rn(U, __dsub_rn(z.x[i], z.x[i + 1])) > __dmul_rn(d, 1.0 + 1e-12)) {
+            // rejected: next attempt
+        } else if (y < exp(-x)) {
+            return x;
+        }
         if (have == 0) {
             ++s;
             extra = philox4x32_10(j, particle | (s << 16), lane, m, k0, k1);
