@@ -62,8 +62,8 @@ ZIG_FLOPS = 1.0 + P_WEDGE * (3.0 + FP64_FLOPS_EXP) + P_TAIL * (1.0 + FP64_FLOPS_
 
 # DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on the 152-theta
-# case of the same kernel (0.709 MB) scaled by the filters processed (x 4096/152).
-FILTER_TRAFFIC_BYTES = 19.1e6
+# case of the same kernel (0.383 MB) scaled by the filters processed (x 4096/152).
+FILTER_TRAFFIC_BYTES = 10.3e6
 
 
 def flops_per_event(R: int) -> float:
@@ -372,7 +372,7 @@ def main() -> None:
             "gpu_launches": 2 * a.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
-                         "traffic": None,
+                         "traffic": FILTER_TRAFFIC_BYTES if w.name == WORKLOAD and w.M == 4096 else None,
                          "kernel": "filter_kernel (FP64 pipe)",
                          "flops_per_event": fpe,
                          "fp64_ops_per_event": ops_per_event(w.R),
