@@ -207,9 +207,6 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
             draws = active ? sh.rem_draws[src][threadIdx.x] : 0u;
             load_x(active);
         }
-        // the Philox block of the lane's next draw, computed one step ahead so
-        // that its integer work overlaps the previous step's FP64 chain
-        Philox4 wnext = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow, key0, key1);
         const int dst = src ^ 1;
         const bool may_park = remaining > 32;
         uint32_t mask = all;  // propensities to (re)compute before the next step
@@ -299,14 +296,14 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 sh.status = PF_ST_BUDGET;
                 done = true;
             } else {
-                const Philox4 w = wnext;
+                const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow,
+                                                key0, key1);
                 const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
                 const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
                 // tau = E / a0 with E ~ Exp(1) from the ziggurat
                 const double E = zig_exp(r0, draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
                                          key1, sh.zig, sh.logt);
                 ++draws;
-                wnext = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow, key0, key1);
                 const double tau = __ddiv_rn(E, a0);
                 const double t_next = __dadd_rn(t, tau);
                 if (dbits(t_next) > t_end_bits) {
@@ -361,7 +358,6 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 t = t_prev;
                 draws = 0;
                 mask = all;
-                wnext = philox4x32_10(0u, static_cast<uint32_t>(L.j), lane, mrow, key0, key1);
             }
         }
         __syncthreads();
