@@ -44,14 +44,16 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = FP64_FLOPS_PER_SM_CLK * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
 # FP64 cost of the SSA event's variate and division, counted by ncu's FP64
 # instruction counters on the pf_fp64_probe kernels (FMA = 2 flops):
-#   IEEE division: 7 DFMA + 1 DMUL = 8 operations, 15 flops;
+#   the kernels' division (approximate-reciprocal seed, third-order Newton
+#   step, residual-corrected quotient): 5 DFMA + 1 DMUL = 6 operations,
+#   11 flops (the IEEE division would take 7 DFMA + 1 DMUL = 8, 15 flops);
 #   exp(): 14 DFMA + 2 DADD = 16 operations, 30 flops;
 #   the table-driven -log(u): 6 DFMA + 2 DMUL + 4 DADD = 12 operations, 18 flops.
 # The Exp(1) variate is a 1024-layer ziggurat: one multiply when the fast path
 # accepts; with probability P_WEDGE a wedge test (3 operations + exp), with
 # probability P_TAIL the tail (log + 1 add).  P_WEDGE + P_TAIL = 1 - mean of
 # x_{i+1}/x_i over the layers = 0.006423; P_TAIL = (1/1024) / (r + 1).
-FP64_OPS_DIV, FP64_FLOPS_DIV = 8.0, 15.0
+FP64_OPS_DIV, FP64_FLOPS_DIV = 6.0, 11.0
 FP64_OPS_EXP, FP64_FLOPS_EXP = 16.0, 30.0
 FP64_OPS_LOG, FP64_FLOPS_LOG = 12.0, 18.0
 P_TAIL = (1.0 / 1024) / (9.2561645442655436867 + 1.0)
@@ -62,8 +64,9 @@ ZIG_FLOPS = 1.0 + P_WEDGE * (3.0 + FP64_FLOPS_EXP) + P_TAIL * (1.0 + FP64_FLOPS_
 
 # DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on the 152-theta
-# case of the same kernel (0.383 MB) scaled by the filters processed (x 4096/152).
-FILTER_TRAFFIC_BYTES = 10.3e6
+# case of the same kernel scaled by the filters processed (x 4096/152); None
+# until taken on the current kernel.
+FILTER_TRAFFIC_BYTES = None
 
 
 def flops_per_event(R: int) -> float:
@@ -421,7 +424,8 @@ def fp64_probe(pf) -> dict:
     iters = {0: 4096, 1: 256, 2: 512}
     iters[3] = 512
     iters[4] = 512
-    for kind in (0, 1, 2, 3, 4):
+    iters[5] = 512
+    for kind in (0, 1, 2, 3, 4, 5):
         pf.pf_fp64_probe(kind, blocks, threads, 16)          # warm-up
         ms, _ = pf.pf_fp64_probe(kind, blocks, threads, iters[kind])
         res[kind] = ms
@@ -431,7 +435,10 @@ def fp64_probe(pf) -> dict:
     div_rate = ops * iters[2] / (res[2] * 1e-3)
     mylog_rate = ops * iters[3] / (res[3] * 1e-3)
     exp_rate = ops * iters[4] / (res[4] * 1e-3)
+    fdiv_rate = ops * iters[5] / (res[5] * 1e-3)
     return {
+        "fast_div_per_s": fdiv_rate,
+        "fast_div_fma_equiv_flops": 2 * fma_rate / fdiv_rate - 2.0,
         "exp_per_s": exp_rate,
         "exp_fma_equiv_flops": 2 * fma_rate / exp_rate - 2.0,
         "table_log_per_s": mylog_rate,

@@ -327,7 +327,9 @@ int pf_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, in
  *   kind 2: IEEE division plus two additions per chain step;
  *   kind 3: the library's table-driven -log(u) (pf_neg_log_u53) plus one
  *           addition per chain step;
- *   kind 4: exp() plus two additions per chain step.
+ *   kind 4: exp() plus two additions per chain step;
+ *   kind 5: the kernels' waiting-time division (see pf_div_check) plus two
+ *           additions per chain step.
  * With ncu's FP64 instruction counters this prices one log() and one division
  * in FP64 operations, the per-event cost model of the SSA kernel's roofline.
  * Returns PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.  Allocates and frees its
@@ -355,6 +357,15 @@ int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n);
  * synchronous.  Returns PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.
  */
 int pf_exp_variates(uint64_t seed, int64_t n, double *out);
+
+/*
+ * pf_div_check -- test support for the SSA waiting time tau = E / a0: over n
+ * pseudo-random (E, a0) pairs, counts the quotients where the kernels'
+ * division (reciprocal seed, one Newton step, residual-corrected quotient)
+ * differs from the IEEE quotient.  Synchronous.  PF_OK, PF_EINVAL, PF_ENOMEM
+ * or PF_ECUDA.
+ */
+int pf_div_check(uint64_t seed, int64_t n, uint64_t *mismatches);
 
 #ifdef __cplusplus
 }

@@ -304,7 +304,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 const double E = zig_exp(r0, draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
                                          key1, sh.zig, sh.logt);
                 ++draws;
-                const double tau = __ddiv_rn(E, a0);
+                const double tau = div_pos(E, a0);
                 const double t_next = __dadd_rn(t, tau);
                 if (dbits(t_next) > t_end_bits) {
                     done = true;                               // the event lies past t_end

@@ -52,6 +52,13 @@ __global__ void probe_kernel(int kind, int64_t iters, double *out) {
                 acc[c] = __dadd_rn(acc[c], __ddiv_rn(1.5, x[c]));
                 x[c] = __dadd_rn(x[c], 1e-12);
             }
+    } else if (kind == 5) {
+        for (int64_t i = 0; i < iters; ++i)
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) {
+                acc[c] = __dadd_rn(acc[c], pf::div_pos(1.5, x[c]));
+                x[c] = __dadd_rn(x[c], 1e-12);
+            }
     } else {
         uint64_t v[kChains];
 #pragma unroll
@@ -74,7 +81,7 @@ __global__ void probe_kernel(int kind, int64_t iters, double *out) {
 
 extern "C" int pf_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters,
                              double *elapsed_ms, double *checksum) {
-    if (kind < 0 || kind > 4 || blocks < 1 || threads < 32 || threads > 1024 || iters < 1 ||
+    if (kind < 0 || kind > 5 || blocks < 1 || threads < 32 || threads > 1024 || iters < 1 ||
         !elapsed_ms)
         return PF_EINVAL;
     double *d = nullptr;
@@ -157,5 +164,41 @@ extern "C" int pf_exp_variates(uint64_t seed, int64_t n, double *out) {
     exp_variates_kernel<<<static_cast<unsigned>((n + 255) / 256), 256>>>(seed, n, zig, d);
     cudaError_t e = cudaMemcpy(out, d, n * sizeof(double), cudaMemcpyDeviceToHost);
     cudaFree(d);
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}
+
+namespace {
+// Counts quotients where div_pos differs from the IEEE division, over n
+// pseudo-random pairs (numerators like Exp(1) variates, divisors spread over
+// 2^-60 .. 2^60).
+__global__ void div_check_kernel(uint64_t seed, int64_t n, unsigned long long *mismatch) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    unsigned long long local = 0;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const pf::Philox4 w = pf::philox4x32_10(static_cast<uint32_t>(k), static_cast<uint32_t>(k >> 32),
+                                                0x5EEDu, 0u, static_cast<uint32_t>(seed),
+                                                static_cast<uint32_t>(seed >> 32));
+        const uint64_t a = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+        const uint64_t b = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
+        const double num = 20.0 * pf::scaled_u53((a >> 11) + 1ull);
+        const int e = static_cast<int>(b & 127u) - 60;
+        const double den = ldexp(1.0 + pf::scaled_u53((b >> 11) + 1ull), e);
+        if (__double_as_longlong(pf::div_pos(num, den)) != __double_as_longlong(__ddiv_rn(num, den)))
+            ++local;
+    }
+    if (local) atomicAdd(mismatch, local);
+}
+}  // namespace
+
+extern "C" int pf_div_check(uint64_t seed, int64_t n, uint64_t *mismatches) {
+    if (n < 0 || !mismatches) return PF_EINVAL;
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) return PF_ENOMEM;
+    cudaMemset(d, 0, sizeof(unsigned long long));
+    div_check_kernel<<<152 * 8, 256>>>(seed, n, d);
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    *mismatches = h;
     return e == cudaSuccess ? PF_OK : PF_ECUDA;
 }

@@ -29,7 +29,7 @@ PF_SCHED_AUTO, PF_SCHED_NATURAL, PF_SCHED_HEAVY_FIRST = 0, 1, 2
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",
             "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit", "pf_poll", "pf_ctx_stats",
-            "pf_ctx_destroy", "pf_exp_variates"]
+            "pf_ctx_destroy", "pf_exp_variates", "pf_div_check"]
 
 
 class PfError(RuntimeError):
@@ -94,6 +94,8 @@ def load():
             lib.pf_neg_log_u53.restype = ct.c_int
             lib.pf_exp_variates.argtypes = [ct.c_uint64, ct.c_int64, P]
             lib.pf_exp_variates.restype = ct.c_int
+            lib.pf_div_check.argtypes = [ct.c_uint64, ct.c_int64, ct.POINTER(ct.c_uint64)]
+            lib.pf_div_check.restype = ct.c_int
             lib.pf_loglik_noalloc.argtypes = [ct.POINTER(pf_network), P, ct.c_int64, ct.c_int32,
                                               P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P,
                                               ct.c_int32, ct.c_uint64, P, P, ct.c_uint64, P]
@@ -263,6 +265,14 @@ def pf_exp_variates(seed: int, n: int) -> np.ndarray:
     out = np.empty(int(n), np.float64)
     _check(lib.pf_exp_variates(ct.c_uint64(int(seed)), int(n), _hptr(out)), "pf_exp_variates")
     return out
+
+
+def pf_div_check(seed: int, n: int) -> int:
+    """Number of the kernels' waiting-time quotients differing from IEEE division."""
+    lib = load()
+    m = ct.c_uint64()
+    _check(lib.pf_div_check(ct.c_uint64(int(seed)), int(n), ct.byref(m)), "pf_div_check")
+    return int(m.value)
 
 
 def pf_neg_log_u53(v) -> np.ndarray:

@@ -73,3 +73,11 @@ def test_exp_variates_match_oracle_bit_for_bit(pf):
     diff = np.flatnonzero(g != o)
     assert len(diff) == 0, (diff[:5], g[diff[:5]], o[diff[:5]])
     assert (g > 9.2561645442655436867).any()   # the tail branch was exercised
+
+
+def test_waiting_time_division_matches_ieee(pf):
+    """The kernels divide E / a0 with a reciprocal seed, one Newton step and a
+    residual correction; over 10^8 pairs it must agree with the IEEE quotient
+    everywhere (a disagreement needs the exact quotient within ~2^-40 of a
+    rounding midpoint)."""
+    assert pf.pf_div_check(7, 100_000_000) == 0
