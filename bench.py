@@ -49,17 +49,20 @@ FP64_PEAK_TFLOPS = FP64_FLOPS_PER_SM_CLK * N_SMS * SM_MAX_MHZ * 1e6 / 1e12
 #   11 flops (the IEEE division would take 7 DFMA + 1 DMUL = 8, 15 flops);
 #   exp(): 14 DFMA + 2 DADD = 16 operations, 30 flops;
 #   the table-driven -log(u): 6 DFMA + 2 DMUL + 4 DADD = 12 operations, 18 flops.
-# The Exp(1) variate is a 1024-layer ziggurat: one multiply when the fast path
-# accepts; with probability P_WEDGE a wedge test (3 operations + exp), with
-# probability P_TAIL the tail (log + 1 add).  P_WEDGE + P_TAIL = 1 - mean of
-# x_{i+1}/x_i over the layers = 0.006423; P_TAIL = (1/1024) / (r + 1).
+# The Exp(1) variate is a 2048-layer ziggurat: one multiply when the fast path
+# accepts; with probability P_WEDGE a wedge test (y: 2 operations; d and the two
+# bounding lines: 3; exp() in the 0.62 % of wedge tests the lines leave open;
+# a rejected attempt, half of them, costs one more multiply), with probability
+# P_TAIL the tail (log + 1 add).  P_WEDGE + P_TAIL = 1 - mean of x_{i+1}/x_i
+# over the layers = 0.003420; P_TAIL = (1/2048) / (r + 1).
 FP64_OPS_DIV, FP64_FLOPS_DIV = 6.0, 11.0
 FP64_OPS_EXP, FP64_FLOPS_EXP = 16.0, 30.0
 FP64_OPS_LOG, FP64_FLOPS_LOG = 12.0, 18.0
-P_TAIL = (1.0 / 1024) / (9.2561645442655436867 + 1.0)
-P_WEDGE = 0.006423 - P_TAIL
-ZIG_OPS = 1.0 + P_WEDGE * (3.0 + FP64_OPS_EXP) + P_TAIL * (1.0 + FP64_OPS_LOG)
-ZIG_FLOPS = 1.0 + P_WEDGE * (3.0 + FP64_FLOPS_EXP) + P_TAIL * (1.0 + FP64_FLOPS_LOG)
+P_TAIL = (1.0 / 2048) / (10.02289706840504086041 + 1.0)
+P_WEDGE = 0.003420 - P_TAIL
+P_WEDGE_OPEN = 0.0062
+ZIG_OPS = 1.0 + P_WEDGE * (5.0 + P_WEDGE_OPEN * FP64_OPS_EXP + 0.5) + P_TAIL * (1.0 + FP64_OPS_LOG)
+ZIG_FLOPS = 1.0 + P_WEDGE * (7.0 + P_WEDGE_OPEN * FP64_FLOPS_EXP + 0.5) + P_TAIL * (1.0 + FP64_FLOPS_LOG)
 
 
 # DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression

@@ -27,7 +27,7 @@
  *     the resampling uniform of interval k uses particle lane 0xFFFFFFFF;
  *   - the waiting time's exponential variate E (tau = E / a0) comes from the
  *     ziggurat method of Marsaglia & Tsang ("The ziggurat method for
- *     generating random variables", J. Stat. Softw. 5(8), 2000) with 1024
+ *     generating random variables", J. Stat. Softw. 5(8), 2000) with 2048
  *     layers (r and v solved from their equations for that layer count); see
  *     exp_variate() for the words it consumes; u2 = (w3:w2 >> 11) 2^-53 in
  *     [0,1) selects the reaction;
@@ -89,16 +89,16 @@ static void draw4(uint64_t seed, uint32_t j, uint32_t i, uint32_t lane, uint32_t
 
 /* ------------------------------------------------------------------------ */
 /* Exponential variates by the ziggurat method (Marsaglia & Tsang 2000).      */
-/* Layers i = 0..1023 of equal area v under f(x) = exp(-x): x_1 = r,          */
-/* x_{i+1} = -log(v / x_i + f(x_i)), x_1024 = 0, and the base layer's virtual */
+/* Layers i = 0..2047 of equal area v under f(x) = exp(-x): x_1 = r,          */
+/* x_{i+1} = -log(v / x_i + f(x_i)), x_2048 = 0, and the base layer's virtual */
 /* width x_0 = v / f(r) (base strip [0, r] plus the tail beyond r).           */
-/* r is the root of the condition x_1024 = 0 with v = (r + 1) exp(-r) (the    */
+/* r is the root of the condition x_2048 = 0 with v = (r + 1) exp(-r) (the    */
 /* base layer's area), solved once in 50-digit arithmetic; the same equations */
 /* give the paper's published r = 7.69711747013104972 for 256 layers.         */
 /* ------------------------------------------------------------------------ */
-#define ZIG_N 1024
-static const double zig_r = 9.2561645442655436867;
-static const double zig_v = 0.00097967899066202091684;
+#define ZIG_N 2048
+static const double zig_r = 10.02289706840504086041;
+static const double zig_v = 0.0004891103607436302956561;
 static double zig_x[ZIG_N + 1], zig_f[ZIG_N + 1];
 static int zig_ready = 0;
 
@@ -134,7 +134,7 @@ static uint64_t next_word(word_stream *ws) {
     return ((uint64_t)ws->w[3] << 32) | ws->w[2];
 }
 
-/* E ~ Exp(1).  Each attempt takes one word: layer i = its low 10 bits,
+/* E ~ Exp(1).  Each attempt takes one word: layer i = its low 11 bits,
  * u = (word >> 11) 2^-53, x = u x_i.  Accept x if x < x_{i+1}; else the base
  * layer returns r plus an Exp(1) tail variate -log(u'), u' = ((w >> 11) + 1)
  * 2^-53 from the next word; other layers accept x if
@@ -143,7 +143,7 @@ static uint64_t next_word(word_stream *ws) {
 static double exp_variate(uint64_t first_word, word_stream *ws) {
     uint64_t W = first_word;
     for (;;) {
-        int i = (int)(W & 0x3FF);
+        int i = (int)(W & 0x7FF);
         double u = (double)(W >> 11) * 0x1p-53;
         double x = u * zig_x[i];
         if (x < zig_x[i + 1]) return x;

@@ -97,6 +97,9 @@ int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P,
         for (int r2 = 0; r2 < R; ++r2)
             if ((mask >> r2) & 1u) t.dep_list[r][t.n_dep[r]++] = (int8_t)r2;
     }
+    t.n_nz = 0;
+    for (int r = 0; r < R; ++r)
+        if (t.sp_a[r] >= 0) t.nz_list[t.n_nz++] = (int8_t)r;
     for (int u = 0; u < U; ++u) {
         if (x0[u] < 0) return fail(PF_EINVAL, "x0[%d] = %d < 0", u, x0[u]);
         t.x0[u] = x0[u];

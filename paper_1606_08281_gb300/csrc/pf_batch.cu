@@ -100,8 +100,8 @@ batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *ite
     __shared__ unsigned long long cur;
     __shared__ uint64_t item;
     __shared__ const ProblemDev *loaded;
-    load_log_table(sh.logt);
     load_zig_table(sh.zig, zig);
+    if (threadIdx.x == 0) sh.zig_g = zig;
     if (threadIdx.x == 0) loaded = nullptr;
     const long long begin = hdr->group_begin[group];
     const unsigned long long count = static_cast<unsigned long long>(hdr->group_count[group]);

@@ -61,8 +61,8 @@ struct SharedHead {
     double rem_t[2][kMaxRemnants];       // its time
     int bucket[16];
     float rate_f[PF_MAX_REACTIONS];  // FP32 copy of rate[], for cost estimates only
-    LogTab logt;
-    ZigTab zig;
+    ZigX zig;                 // ziggurat layer edges
+    const ZigTab *zig_g;      // the full ziggurat table (global memory)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -227,50 +227,58 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 break;
             }
             if (!active) continue;
-            if constexpr (kDepList) {
-                // large networks: each lane recomputes only its own dependent
-                // reactions (a full refill when mask is `all`); a trip issues
-                // max-over-lanes(#dependents) multiplies instead of one per
-                // reaction any lane needs
-                if (mask == all) {
-                    for (int r = 0; r < R; ++r) a[r] = propensity<UM>(r, sh, L);
-                } else {
-                    const int c = static_cast<int>(mask);  // the fired reaction (see below)
-                    const int nd = sh.net.n_dep[c];
+            if constexpr (kDepList || kHoist) {
+                // Each lane recomputes its own list of propensities: the fired
+                // reaction's dependents, or (a particle just taken from the
+                // pool, mask == `all`) every reaction with reactants, after
+                // setting the zero-order ones to their rates.  Both cases run
+                // the same loop, so a trip issues max-over-lanes(list length)
+                // multiplies instead of a dependents pass plus a divergent
+                // refill pass.
+                const bool refill = mask == all;
+                const int c = refill ? 0 : static_cast<int>(mask);
+                const int nd = refill ? sh.net.n_nz : sh.net.n_dep[c];
+                const int8_t *lst = refill ? sh.net.nz_list : sh.net.dep_list[c];
+                if constexpr (kHoist) {
+                    if (refill) {
+#pragma unroll
+                        for (int q = 0; q < RM; ++q)
+                            if ((desc_reg[q] & 0xFF) == 0) a[q] = rate_reg[q];
+                    }
                     for (int i = 0; i < nd; ++i) {
-                        const int r = sh.net.dep_list[c][i];
+                        const int r = lst[i];
+                        double rate = rate_reg[0];
+                        int desc = desc_reg[0];
+#pragma unroll
+                        for (int q = 1; q < (kHoist ? RM : 1); ++q) {
+                            rate = r == q ? rate_reg[q] : rate;
+                            desc = r == q ? desc_reg[q] : desc;
+                        }
+                        const double v = propensity_reg<UM>(rate, desc, L);
+#pragma unroll
+                        for (int q = 0; q < RM; ++q) a[q] = r == q ? v : a[q];
+                    }
+                } else {
+                    if (refill) {
+                        for (int r = 0; r < R; ++r)
+                            if (sh.net.sp_a[r] < 0) a[r] = sh.rate[r];
+                    }
+                    for (int i = 0; i < nd; ++i) {
+                        const int r = lst[i];
                         a[r] = propensity<UM>(r, sh, L);
                     }
                 }
-            } else if (kHoist && mask != all) {
-                // small networks: the fired reaction's dependents one by one,
-                // written into the register array through select chains
-                const int c = static_cast<int>(mask);
-                const int nd = sh.net.n_dep[c];
-                for (int i = 0; i < nd; ++i) {
-                    const int r = sh.net.dep_list[c][i];
-                    double rate = rate_reg[0];
-                    int desc = desc_reg[0];
-#pragma unroll
-                    for (int q = 1; q < (kHoist ? RM : 1); ++q) {
-                        rate = r == q ? rate_reg[q] : rate;
-                        desc = r == q ? desc_reg[q] : desc;
-                    }
-                    const double v = (desc & 0xFF) == 0 ? rate : propensity_reg<UM>(rate, desc, L);
-#pragma unroll
-                    for (int q = 0; q < RM; ++q) a[q] = r == q ? v : a[q];
-                }
             } else {
+                // mid-size networks with the state in shared memory: the
+                // reactions of `mask`, each multiply issued once per trip
 #pragma unroll
                 for (int r = 0; r < RM; ++r) {
                     // a zero-order reaction's propensity is its rate exactly (theta * 1.0):
                     // a warp-uniform test skips the multiply for it
-                    const bool zero_order = kHoist ? (desc_reg[r] & 0xFF) == 0 : sh.net.sp_a[r] < 0;
-                    if (zero_order) {
-                        if ((mask >> r) & 1u) a[r] = kHoist ? rate_reg[r] : sh.rate[r];
+                    if (sh.net.sp_a[r] < 0) {
+                        if ((mask >> r) & 1u) a[r] = sh.rate[r];
                     } else if ((mask >> r) & 1u) {
-                        if constexpr (kHoist) a[r] = propensity_reg<UM>(rate_reg[r], desc_reg[r], L);
-                        else a[r] = propensity<UM>(r, sh, L);
+                        a[r] = propensity<UM>(r, sh, L);
                     }
                 }
             }
@@ -302,7 +310,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
                 // tau = E / a0 with E ~ Exp(1) from the ziggurat
                 const double E = zig_exp(r0, draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
-                                         key1, sh.zig, sh.logt);
+                                         key1, sh.zig, sh.zig_g);
                 ++draws;
                 const double tau = div_pos(E, a0);
                 const double t_next = __dadd_rn(t, tau);

@@ -52,8 +52,8 @@ __global__ void __launch_bounds__(128, 4) filter_kernel(const FilterArgs args) {
         uint32_t *dst = reinterpret_cast<uint32_t *>(&sh.net);
         for (int i = tid; i < static_cast<int>(sizeof(NetTables) / 4); i += B) dst[i] = src[i];
     }
-    load_log_table(sh.logt);
     load_zig_table(sh.zig, args.zig);
+    if (tid == 0) sh.zig_g = args.zig;
     __syncthreads();
     FilterJob job;
     job.theta = args.thetas + mrow * args.net.d;
@@ -92,8 +92,8 @@ __global__ void __launch_bounds__(128, 4) filter_kernel_global(const FilterArgs 
         uint32_t *dst = reinterpret_cast<uint32_t *>(&sh.net);
         for (int i = tid; i < static_cast<int>(sizeof(NetTables) / 4); i += B) dst[i] = src[i];
     }
-    load_log_table(sh.logt);
     load_zig_table(sh.zig, args.zig);
+    if (tid == 0) sh.zig_g = args.zig;
     unsigned char *arrays = slabs + static_cast<size_t>(blockIdx.x) * slab_bytes;
     const int64_t F = args.M * T;
     for (int64_t slot = blockIdx.x; slot < F; slot += gridDim.x) {
@@ -345,14 +345,23 @@ int launch_schedule(const FilterArgs &a, uint32_t *cost, uint32_t *order, uint32
 static __device__ ZigTab g_zig_table;
 
 // The ziggurat table, written from its recurrence with the host C library's
-// exp and log (x_1 = r, x_{i+1} = -log(v / x_i + exp(-x_i)), x_256 = 0,
-// x_0 = v / exp(-r), f_i = exp(-x_i)).
+// exp and log (x_1 = r, x_{i+1} = -log(v / x_i + exp(-x_i)), x_2048 = 0,
+// x_0 = v / exp(-r), f_i = exp(-x_i)), and each wedge's bounding lines.
 static void build_zig_table(ZigTab &t) {
     t.x[0] = kZigV / std::exp(-kZigR);
     t.x[1] = kZigR;
     for (int i = 1; i < kZigLayers - 1; ++i) t.x[i + 1] = -std::log(kZigV / t.x[i] + std::exp(-t.x[i]));
     t.x[kZigLayers] = 0.0;
-    for (int i = 0; i <= kZigLayers; ++i) t.f[i] = std::exp(-t.x[i]);
+    for (int i = 0; i < kZigLayers; ++i) {
+        const double f = std::exp(-t.x[i]), f1 = std::exp(-t.x[i + 1]);
+        const double m = std::ldexp(f1, -48);
+        ZigLayer &L = t.layer[i];
+        L.f = f;
+        L.df = f1 - f;
+        L.lo = f - m;
+        L.hi = f + m;
+        L.slope = i == 0 ? 0.0 : L.df / (t.x[i] - t.x[i + 1]);
+    }
 }
 
 const ZigTab *zig_table_device(int *err) {

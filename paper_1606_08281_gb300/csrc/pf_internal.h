@@ -12,7 +12,9 @@ struct ZigTab;
 // (species, order) pairs because the total order is <= 2 (sp = -1: none).
 // Change side: a compact list of (species, delta) per reaction.  dep[r] has
 // bit r' set when reaction r' reads a species that reaction r changes, so
-// only those propensities are recomputed after r fires.
+// only those propensities are recomputed after r fires; nz_list names the
+// reactions whose propensity depends on the state at all (the others' is
+// their rate), i.e. what a particle taken from the pool computes first.
 struct NetTables {
     int32_t U, R, P, d;
     int32_t rate_col[PF_MAX_REACTIONS];
@@ -24,6 +26,8 @@ struct NetTables {
     uint32_t dep[PF_MAX_REACTIONS];
     int8_t n_dep[PF_MAX_REACTIONS];                      // popcount of dep[r]
     int8_t dep_list[PF_MAX_REACTIONS][PF_MAX_REACTIONS]; // the reactions of dep[r], ascending
+    int8_t n_nz;                                         // reactions with reactants
+    int8_t nz_list[PF_MAX_REACTIONS];                    // those reactions, ascending
     int32_t x0[PF_MAX_SPECIES];
     double C[PF_MAX_OBS_DIM][PF_MAX_SPECIES];
     double sigma[PF_MAX_OBS_DIM];

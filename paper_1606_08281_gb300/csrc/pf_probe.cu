@@ -139,9 +139,7 @@ extern "C" int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n) {
 
 namespace {
 __global__ void exp_variates_kernel(uint64_t seed, int64_t n, const pf::ZigTab *zig, double *out) {
-    __shared__ pf::LogTab lt;
-    __shared__ pf::ZigTab zt;
-    pf::load_log_table(lt);
+    __shared__ pf::ZigX zt;
     pf::load_zig_table(zt, zig);
     __syncthreads();
     const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -149,7 +147,7 @@ __global__ void exp_variates_kernel(uint64_t seed, int64_t n, const pf::ZigTab *
     const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
     const pf::Philox4 w = pf::philox4x32_10(static_cast<uint32_t>(k), 0u, 0u, 0u, k0, k1);
     const uint64_t first = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
-    out[k] = pf::zig_exp(first, static_cast<uint32_t>(k), 0u, 0u, 0u, k0, k1, zt, lt);
+    out[k] = pf::zig_exp(first, static_cast<uint32_t>(k), 0u, 0u, 0u, k0, k1, zt, zig);
 }
 }  // namespace
 

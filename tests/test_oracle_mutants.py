@@ -19,7 +19,7 @@ MUTANTS = {
     "time_times_a0": ("double tau = E / a0;", "double tau = E * a0;", "birth_death_law"),
     "ziggurat_no_wedge_test": ("if (y < exp(-x)) return x;", "return x;", "exp_law"),
     "ziggurat_tail_without_offset": ("return zig_r + -log(u1);", "return -log(u1);", "exp_law"),
-    "ziggurat_layer_bits": ("int i = (int)(W & 0x3FF);", "int i = (int)(W & 0x1FF);", "exp_law"),
+    "ziggurat_layer_bits": ("int i = (int)(W & 0x7FF);", "int i = (int)(W & 0x3FF);", "exp_law"),
     "stoichiometry_sign": ("x[u] += net->prod[chosen * net->U + u] - net->reac[chosen * net->U + u];",
                            "x[u] += net->reac[chosen * net->U + u] - net->prod[chosen * net->U + u];",
                            "birth_death_law"),
