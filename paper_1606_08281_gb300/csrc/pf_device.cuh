@@ -213,18 +213,20 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
         for (;;) {
             const unsigned busy = __ballot_sync(kFull, active);
             if (busy == 0) break;
-            // lane 0's view of the pool counter, so that the whole warp decides alike
-            const int pool_now =
-                __shfl_sync(kFull, *reinterpret_cast<volatile int *>(&sh.pool_next), 0);
-            if (may_park && __popc(busy) < kParkLanes && pool_now >= N) {
-                if (active) {
-                    const int slot = atomicAdd(&sh.rem_n[dst], 1);
-                    sh.rem_j[dst][slot] = L.j;
-                    sh.rem_t[dst][slot] = t;
-                    sh.rem_draws[dst][slot] = draws;
-                    store_x();
+            if (may_park && __popc(busy) < kParkLanes) {
+                // lane 0's view of the pool counter, so that the whole warp decides alike
+                const int pool_now =
+                    __shfl_sync(kFull, *reinterpret_cast<volatile int *>(&sh.pool_next), 0);
+                if (pool_now >= N) {
+                    if (active) {
+                        const int slot = atomicAdd(&sh.rem_n[dst], 1);
+                        sh.rem_j[dst][slot] = L.j;
+                        sh.rem_t[dst][slot] = t;
+                        sh.rem_draws[dst][slot] = draws;
+                        store_x();
+                    }
+                    break;
                 }
-                break;
             }
             if (!active) continue;
             if constexpr (kDepList || kHoist) {
@@ -310,7 +312,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
                 // tau = E / a0 with E ~ Exp(1) from the ziggurat
                 const double E = zig_exp(r0, draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
-                                         key1, sh.zig, sh.zig_g);
+                                         key1, sh.zig.x, sh.zig_g);
                 ++draws;
                 const double tau = div_pos(E, a0);
                 const double t_next = __dadd_rn(t, tau);

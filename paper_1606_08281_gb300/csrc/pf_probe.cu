@@ -147,7 +147,7 @@ __global__ void exp_variates_kernel(uint64_t seed, int64_t n, const pf::ZigTab *
     const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
     const pf::Philox4 w = pf::philox4x32_10(static_cast<uint32_t>(k), 0u, 0u, 0u, k0, k1);
     const uint64_t first = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
-    out[k] = pf::zig_exp(first, static_cast<uint32_t>(k), 0u, 0u, 0u, k0, k1, zt, zig);
+    out[k] = pf::zig_exp(first, static_cast<uint32_t>(k), 0u, 0u, 0u, k0, k1, zt.x, zig);
 }
 }  // namespace
 

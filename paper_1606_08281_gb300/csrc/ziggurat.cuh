@@ -55,14 +55,15 @@ struct ZigX {
 // Exp(1) variate of one draw.  Words, in order: `first` (w1:w0 of the draw's
 // Philox block, counter (j, particle, lane, m)); then for s = 1, 2, ... the
 // words w1:w0 and w3:w2 of the block with counter (j, particle | s << 16,
-// lane, m).  Each attempt takes one word: layer i = low 11 bits,
+// lane, m).  zx points at the layer edges x_0..x_2048 (a shared-memory copy
+// or the table's own).  Each attempt takes one word: layer i = low 11 bits,
 // u = (word >> 11) 2^-53, x = u x_i; x < x_{i+1} accepts; the base layer
 // otherwise returns r - log(u'), u' = ((next >> 11) + 1) 2^-53; other layers
 // accept x when f_i + U (f_{i+1} - f_i) < exp(-x), U = (next >> 11) 2^-53, and
 // otherwise retry with the next word.
 __device__ __forceinline__ double zig_exp(uint64_t first, uint32_t j, uint32_t particle,
                                           uint32_t lane, uint32_t m, uint32_t k0, uint32_t k1,
-                                          const ZigX &zx, const ZigTab *__restrict__ zg) {
+                                          const double *zx, const ZigTab *__restrict__ zg) {
     uint64_t W = first;
     uint32_t s = 0;
     Philox4 extra{0, 0, 0, 0};
@@ -70,10 +71,10 @@ __device__ __forceinline__ double zig_exp(uint64_t first, uint32_t j, uint32_t p
     for (;;) {
         const int i = static_cast<int>(W & 0x7FFu);
         const uint64_t uv = W >> 11;
-        const double xi = zx.x[i];
+        const double xi = zx[i];
         const double x = __dmul_rn(uv ? scaled_u53(uv) : 0.0, xi);
         // both non-negative: compare as integers
-        if (__double_as_longlong(x) < __double_as_longlong(zx.x[i + 1])) return x;
+        if (__double_as_longlong(x) < __double_as_longlong(zx[i + 1])) return x;
         // slow paths need the next word of the stream
         uint64_t W2;
         if (have == 0) {
