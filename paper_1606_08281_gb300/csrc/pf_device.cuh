@@ -229,6 +229,15 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 }
             }
             if (!active) continue;
+            // This draw's random words and the ziggurat's first attempt depend
+            // on the draw counter alone: computed first, they overlap with the
+            // propensities (used only if the step draws at all).
+            const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow,
+                                            key0, key1);
+            const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+            const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
+            double E;
+            const bool fast = zig_fast(r0, sh.zig.x, E);
             if constexpr (kDepList || kHoist) {
                 // Each lane recomputes its own list of propensities: the fired
                 // reaction's dependents, or (a particle just taken from the
@@ -306,40 +315,40 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 sh.status = PF_ST_BUDGET;
                 done = true;
             } else {
-                const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow,
-                                                key0, key1);
-                const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
-                const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
-                // tau = E / a0 with E ~ Exp(1) from the ziggurat
-                const double E = zig_exp(r0, draws, static_cast<uint32_t>(L.j), lane, mrow, key0,
-                                         key1, sh.zig.x, sh.zig_g);
+                // tau = E / a0 with E ~ Exp(1) from the ziggurat (rare slow
+                // path: the whole algorithm again from the first word)
+                if (!fast)
+                    E = zig_exp(r0, draws, static_cast<uint32_t>(L.j), lane, mrow, key0, key1,
+                                sh.zig.x, sh.zig_g);
                 ++draws;
                 const double tau = div_pos(E, a0);
                 const double t_next = __dadd_rn(t, tau);
+                // the reaction, chosen before the time test so that both
+                // chains overlap (it is used only if the event is in time)
+                const uint64_t v2 = r1 >> 11;                  // u2 = v2 2^-53 in [0, 1)
+                const double target = __dmul_rn(v2 ? scaled_u53(v2) : 0.0, a0);
+                const long long tb = dbits(target);
+                int chosen = 0;                                // first r with target < S_r
+                if constexpr (kDepList) {
+                    for (int r = 0; r < R; ++r) chosen += dbits(S[r]) <= tb ? 1 : 0;
+                    if (chosen >= R) {                         // rounding guard
+                        chosen = 0;
+                        for (int r = 0; r < R; ++r)
+                            if (dbits(a[r]) != 0) chosen = r;
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < RM; ++r) chosen += (r < R && dbits(S[r]) <= tb) ? 1 : 0;
+                    if (chosen >= R) {                         // rounding guard
+                        chosen = 0;
+#pragma unroll
+                        for (int r = 0; r < RM; ++r)
+                            if (r < R && dbits(a[r]) != 0) chosen = r;
+                    }
+                }
                 if (dbits(t_next) > t_end_bits) {
                     done = true;                               // the event lies past t_end
                 } else {
-                    const uint64_t v2 = r1 >> 11;              // u2 = v2 2^-53 in [0, 1)
-                    const double target = __dmul_rn(v2 ? scaled_u53(v2) : 0.0, a0);
-                    const long long tb = dbits(target);
-                    int chosen = 0;                            // first r with target < S_r
-                    if constexpr (kDepList) {
-                        for (int r = 0; r < R; ++r) chosen += dbits(S[r]) <= tb ? 1 : 0;
-                        if (chosen >= R) {                     // rounding guard
-                            chosen = 0;
-                            for (int r = 0; r < R; ++r)
-                                if (dbits(a[r]) != 0) chosen = r;
-                        }
-                    } else {
-#pragma unroll
-                        for (int r = 0; r < RM; ++r) chosen += (r < R && dbits(S[r]) <= tb) ? 1 : 0;
-                        if (chosen >= R) {                     // rounding guard
-                            chosen = 0;
-#pragma unroll
-                            for (int r = 0; r < RM; ++r)
-                                if (r < R && dbits(a[r]) != 0) chosen = r;
-                        }
-                    }
                     const int nch = sh.net.n_change[chosen];
                     for (int i = 0; i < nch; ++i) {
                         const int sp = sh.net.ch_sp[chosen][i], dlt = sh.net.ch_delta[chosen][i];

@@ -110,6 +110,15 @@ __device__ __forceinline__ double zig_exp(uint64_t first, uint32_t j, uint32_t p
     }
 }
 
+// The first attempt alone: x = u x_i from the draw's first word, and whether
+// the fast path accepts it (then zig_exp would return the same x).
+__device__ __forceinline__ bool zig_fast(uint64_t first, const double *zx, double &x) {
+    const int i = static_cast<int>(first & 0x7FFu);
+    const uint64_t uv = first >> 11;
+    x = __dmul_rn(uv ? scaled_u53(uv) : 0.0, zx[i]);
+    return __double_as_longlong(x) < __double_as_longlong(zx[i + 1]);
+}
+
 // Copy the layer edges into shared memory (all threads of the block).
 __device__ __forceinline__ void load_zig_table(ZigX &dst, const ZigTab *src) {
     for (int i = threadIdx.x; i <= kZigLayers; i += blockDim.x) dst.x[i] = src->x[i];
