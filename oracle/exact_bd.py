@@ -57,17 +57,24 @@ def transition_closed(k1: float, k2: float, dt: float, nmax: int) -> np.ndarray:
 
 
 def loglik(k1: float, k2: float, x0: int, obs_times, y, c: float = 1.0, sigma: float = 1.0,
-           nmax: int = 200, transition=transition_expm):
+           nmax: int = 200, transition=transition_expm, x0_hi: int | None = None,
+           obs_offset: float = 0.0, obs_var: float = 0.0):
     """Exact (truncated) log p(y | k1, k2) of one trajectory, and the leaked mass.
 
     The forward recursion follows the same factorisation as the paper's filter:
-    log p(y) = sum_k log p(y_k | y_{<k}), Supp. I.
+    log p(y) = sum_k log p(y_k | y_{<k}), Supp. I.  Optional model extensions
+    (the Lac-Gfp example's forms): the initial count uniform on x0..x0_hi, and
+    the emission N(y; obs_offset + c n, sigma^2 + obs_var n).
     """
     obs_times = np.asarray(obs_times, float)
     y = np.asarray(y, float).reshape(-1)
     states = np.arange(nmax + 1)
     alpha = np.zeros(nmax + 1)
-    alpha[x0] = 1.0
+    if x0_hi is None:
+        alpha[x0] = 1.0
+    else:
+        alpha[x0:x0_hi + 1] = 1.0 / (x0_hi - x0 + 1)
+    sd = np.sqrt(sigma ** 2 + obs_var * states)
     t_prev = 0.0
     L = 0.0
     leak = 0.0
@@ -82,7 +89,7 @@ def loglik(k1: float, k2: float, x0: int, obs_times, y, c: float = 1.0, sigma: f
             mass_in = alpha.sum()
             alpha = alpha @ P
             leak += mass_in - alpha.sum()
-        emis = stats.norm.pdf(y[k], loc=c * states, scale=sigma)
+        emis = stats.norm.pdf(y[k], loc=obs_offset + c * states, scale=sd)
         alpha = alpha * emis
         ck = alpha.sum()
         L += np.log(ck)

@@ -41,6 +41,24 @@
  *     q_i = floor(2^32 exp(e_i - max e)), ancestor a_j = min{i : N Q_i > u + j W};
  *   - a particle may make at most `budget` draws per interval; needing more
  *     marks the filter BUDGET and its theta gets log-likelihood -inf.
+ *
+ * Model extensions of the Lac-Gfp example (Supp. "LacGfp example"), each off
+ * when its array is NULL:
+ *   - composed rates: reaction r's rate is sum_c rate_coef[r][c] theta_c
+ *     (e.g. theta_4 + theta_5 [IPTG]), summed over c in order;
+ *   - a random initial state: each particle's count of species u is uniform
+ *     on the integers x0[u]..x0_hi[u] (the paper's U([a, b]) initial
+ *     distributions), one Philox word per (particle, species): counter
+ *     (particle i, 0xFFFFFFFE, (trajectory << 20) | (u >> 2), theta m), word
+ *     u & 3, x = x0[u] + floor(word (x0_hi[u] - x0[u] + 1) / 2^32);
+ *   - a state-dependent observation variance: y_p ~ N(obs_offset_p + (C x)_p,
+ *     v_p) with v_p = sigma_p^2 + sum_u obs_var[p][u] x_u (the paper's
+ *     N(22.85 x, 5.72 sqrt(x)) plus a background, here Gaussian N(offset,
+ *     sigma^2)); the log-weight then carries -1/2 sum_p log v_p per particle,
+ *     and the integer resampling weights are taken from the log-weights
+ *     rounded to multiples of 2^-20 (so that a last-place difference between
+ *     two logarithm implementations cannot move every quantised weight); the
+ *     likelihood itself uses the unrounded log-weights.
  */
 #include <math.h>
 #include <stdint.h>
@@ -180,7 +198,29 @@ typedef struct {
     const int32_t *reac;       /* [R][U] p_ru */
     const int32_t *prod;       /* [R][U] q_ru */
     const int32_t *rate_index; /* [R] or NULL */
+    const double *rate_coef;   /* [R][d] or NULL: composed rates */
+    int32_t d;
 } orc_net;
+
+/* Initial-state and observation extensions (NULL = off). */
+typedef struct {
+    const int32_t *x0_hi;      /* [U] */
+    const double *obs_offset;  /* [P] */
+    const double *obs_var;     /* [P][U] */
+} orc_model;
+
+/* Reaction rates of one theta row: theta[rho(r)], or the composed sums. */
+static void reaction_rates(const orc_net *net, const double *theta, double *rate) {
+    for (int r = 0; r < net->R; r++) {
+        if (net->rate_coef) {
+            double v = 0.0;
+            for (int c = 0; c < net->d; c++) v = v + net->rate_coef[r * net->d + c] * theta[c];
+            rate[r] = v;
+        } else {
+            rate[r] = theta[net->rate_index ? net->rate_index[r] : r];
+        }
+    }
+}
 
 /* binomial coefficient C(x, p) for p in {0,1,2}, exact in int64 */
 static int64_t binom_small(int64_t x, int32_t p) {
@@ -191,7 +231,7 @@ static int64_t binom_small(int64_t x, int32_t p) {
 }
 
 /* Mass-action propensities a_r and their prefix sums S_r, reaction order. */
-static double propensities(const orc_net *net, const double *theta, const int64_t *x,
+static double propensities(const orc_net *net, const double *rate, const int64_t *x,
                            double *a, double *S) {
     double run = 0.0;
     for (int r = 0; r < net->R; r++) {
@@ -200,8 +240,7 @@ static double propensities(const orc_net *net, const double *theta, const int64_
             int32_t p = net->reac[r * net->U + u];
             if (p > 0) h *= binom_small(x[u], p);
         }
-        int col = net->rate_index ? net->rate_index[r] : r;
-        a[r] = theta[col] * (double)h;
+        a[r] = rate[r] * (double)h;
         run = run + a[r];
         S[r] = run;
     }
@@ -213,13 +252,13 @@ static double propensities(const orc_net *net, const double *theta, const int64_
  * lane = (trajectory << 20) | interval; returns ORC_OK or ORC_BUDGET.
  * *fired is increased by the number of reactions that fired.
  */
-static int ssa_advance(const orc_net *net, const double *theta, int64_t *x, double t, double t_end,
+static int ssa_advance(const orc_net *net, const double *rate, int64_t *x, double t, double t_end,
                        uint64_t seed, uint32_t particle, uint32_t lane, uint32_t m,
                        uint64_t budget, double *a, double *S, uint64_t *fired) {
     if (!(t_end > t)) return ORC_OK;
     uint64_t j = 0;
     for (;;) {
-        double a0 = propensities(net, theta, x, a, S);
+        double a0 = propensities(net, rate, x, a, S);
         if (!(a0 > 0.0)) return ORC_OK; /* absorbing state: nothing can fire */
         if (j >= budget) return ORC_BUDGET;
         uint32_t w[4];
@@ -296,11 +335,14 @@ typedef struct {
     uint64_t digest;
 } filter_result;
 
-static int run_filter(const orc_net *net, const double *theta, const int32_t *x0,
-                      const double *obs_times, int K, const double *y_traj /* [K][P] */,
-                      int P, const double *Cm, const double *sigma, int N, uint64_t seed,
-                      uint64_t budget, uint32_t traj, uint32_t m, filter_result *res,
-                      int32_t *final_states /* [N][U] or NULL */) {
+/* Log-weight rounded to a multiple of 2^-20 (exact scaling, ties to even). */
+static double grid20(double e) { return ldexp(nearbyint(ldexp(e, 20)), -20); }
+
+static int run_filter(const orc_net *net, const orc_model *mdl, const double *theta,
+                      const int32_t *x0, const double *obs_times, int K,
+                      const double *y_traj /* [K][P] */, int P, const double *Cm,
+                      const double *sigma, int N, uint64_t seed, uint64_t budget, uint32_t traj,
+                      uint32_t m, filter_result *res, int32_t *final_states /* [N][U] or NULL */) {
     int U = net->U, R = net->R;
     int64_t *x = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * U);
     int64_t *xn = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * U);
@@ -309,17 +351,31 @@ static int run_filter(const orc_net *net, const double *theta, const int32_t *x0
     int32_t *anc = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
     double *a = (double *)malloc(sizeof(double) * (size_t)R);
     double *S = (double *)malloc(sizeof(double) * (size_t)R);
-    if (!x || !xn || !e || !q || !anc || !a || !S) {
-        free(x); free(xn); free(e); free(q); free(anc); free(a); free(S);
+    double *rate = (double *)malloc(sizeof(double) * (size_t)R);
+    if (!x || !xn || !e || !q || !anc || !a || !S || !rate) {
+        free(x); free(xn); free(e); free(q); free(anc); free(a); free(S); free(rate);
         return ORC_ENOMEM;
     }
-    /* log of the Gaussian normalising constant: sum_p log sigma_p + (P/2) log(2 pi) */
+    reaction_rates(net, theta, rate);
+    /* log of the Gaussian normalising constant: sum_p log sigma_p + (P/2) log(2 pi);
+     * with a state-dependent variance the log v_p terms sit in each log-weight */
     double lognorm = 0.0;
-    for (int p = 0; p < P; p++) lognorm = lognorm + log(sigma[p]);
+    if (!mdl->obs_var)
+        for (int p = 0; p < P; p++) lognorm = lognorm + log(sigma[p]);
     lognorm = lognorm + 0.5 * (double)P * log(2.0 * M_PI);
 
+    /* initial particles: x0, or uniform on x0..x0_hi per species */
     for (int i = 0; i < N; i++)
-        for (int u = 0; u < U; u++) x[(size_t)i * U + u] = x0[u];
+        for (int u = 0; u < U; u++) {
+            int64_t v = x0[u];
+            if (mdl->x0_hi) {
+                uint32_t w[4];
+                draw4(seed, (uint32_t)i, 0xFFFFFFFEu, (traj << 20) | (uint32_t)(u >> 2), m, w);
+                uint64_t span = (uint64_t)((int64_t)mdl->x0_hi[u] - x0[u] + 1);
+                v += (int64_t)(((uint64_t)w[u & 3] * span) >> 32);
+            }
+            x[(size_t)i * U + u] = v;
+        }
     double t_prev = 0.0, ll = 0.0, emax = 0.0;
     uint64_t events = 0, digest = 0;
     int status = ORC_OK;
@@ -328,8 +384,12 @@ static int run_filter(const orc_net *net, const double *theta, const int32_t *x0
         uint32_t lane = (traj << 20) | (uint32_t)k;
         /* resample by the weights of observation k-1 (Supp. I, "Sample H indices") */
         if (k >= 1) {
-            for (int i = 0; i < N; i++)
-                q[i] = (uint64_t)ldexp(exp(e[i] - emax), 32);
+            for (int i = 0; i < N; i++) {
+                if (mdl->obs_var)
+                    q[i] = (uint64_t)ldexp(exp(grid20(e[i]) - grid20(emax)), 32);
+                else
+                    q[i] = (uint64_t)ldexp(exp(e[i] - emax), 32);
+            }
             uint32_t w[4];
             draw4(seed, 0u, 0xFFFFFFFFu, lane, m, w);
             uint64_t r64 = ((uint64_t)w[1] << 32) | w[0];
@@ -343,23 +403,34 @@ static int run_filter(const orc_net *net, const double *theta, const int32_t *x0
         /* simulate every particle to the observation time (Supp. I, "Simulate X_t") */
         double t_k = obs_times[k];
         for (int i = 0; i < N && status == ORC_OK; i++)
-            status = ssa_advance(net, theta, &x[(size_t)i * U], t_prev, t_k, seed, (uint32_t)i,
+            status = ssa_advance(net, rate, &x[(size_t)i * U], t_prev, t_k, seed, (uint32_t)i,
                                  lane, m, budget, a, S, &events);
         if (status != ORC_OK) break;
         for (int j = 0; j < N; j++)
             digest += slot_digest((uint32_t)k, (uint32_t)j, (uint32_t)anc[j], &x[(size_t)j * U], U);
-        /* weights l_t^i = N(y_t; C x_t^i, diag sigma^2)  (Supp. I, "Compute l_t^i") */
+        /* weights l_t^i = N(y_t; C x_t^i, diag sigma^2)  (Supp. I, "Compute l_t^i"),
+         * or with the offset mean and state-dependent variance of the model */
         const double *yk = &y_traj[(size_t)k * P];
         for (int i = 0; i < N; i++) {
-            double acc = 0.0;
+            double acc = 0.0, lv = 0.0;
             for (int p = 0; p < P; p++) {
-                double mu = 0.0;
+                double mu = mdl->obs_offset ? mdl->obs_offset[p] : 0.0;
                 for (int u = 0; u < U; u++)
                     mu = mu + Cm[p * U + u] * (double)x[(size_t)i * U + u];
-                double z = (yk[p] - mu) / sigma[p];
-                acc = acc + z * z;
+                if (mdl->obs_var) {
+                    double v = sigma[p] * sigma[p];
+                    for (int u = 0; u < U; u++)
+                        v = v + mdl->obs_var[p * U + u] * (double)x[(size_t)i * U + u];
+                    double dv = yk[p] - mu;
+                    acc = acc + dv * dv / v;
+                    lv = lv + log(v);
+                } else {
+                    double z = (yk[p] - mu) / sigma[p];
+                    acc = acc + z * z;
+                }
             }
-            e[i] = -0.5 * acc;
+            if (mdl->obs_var) e[i] = -0.5 * (acc + lv);
+            else e[i] = -0.5 * acc;
         }
         emax = e[0];
         for (int i = 1; i < N; i++)
@@ -382,7 +453,7 @@ static int run_filter(const orc_net *net, const double *theta, const int32_t *x0
         for (int i = 0; i < N; i++)
             for (int u = 0; u < U; u++)
                 final_states[(size_t)i * U + u] = (int32_t)x[(size_t)i * U + u];
-    free(x); free(xn); free(e); free(q); free(anc); free(a); free(S);
+    free(x); free(xn); free(e); free(q); free(anc); free(a); free(S); free(rate);
     return 0;
 }
 
@@ -396,10 +467,33 @@ static int check_network(const orc_net *net, int d) {
             order += p;
         }
         if (order > 2) return ORC_EINVAL;
-        int col = net->rate_index ? net->rate_index[r] : r;
-        if (col < 0 || col >= d) return ORC_EINVAL;
+        if (net->rate_coef) {
+            for (int c = 0; c < d; c++) {
+                double v = net->rate_coef[r * d + c];
+                if (!(v >= 0.0) || !isfinite(v)) return ORC_EINVAL;
+            }
+        } else {
+            int col = net->rate_index ? net->rate_index[r] : r;
+            if (col < 0 || col >= d) return ORC_EINVAL;
+        }
     }
-    if (!net->rate_index && d < net->R) return ORC_EINVAL;
+    if (!net->rate_coef && !net->rate_index && d < net->R) return ORC_EINVAL;
+    return 0;
+}
+
+static int check_model(const orc_model *mdl, const int32_t *x0, int U, int P) {
+    for (int u = 0; u < U; u++) {
+        if (x0[u] < 0) return ORC_EINVAL;
+        if (mdl->x0_hi && mdl->x0_hi[u] < x0[u]) return ORC_EINVAL;
+    }
+    for (int p = 0; p < P; p++) {
+        if (mdl->obs_offset && !isfinite(mdl->obs_offset[p])) return ORC_EINVAL;
+        if (mdl->obs_var)
+            for (int u = 0; u < U; u++) {
+                double v = mdl->obs_var[p * U + u];
+                if (!(v >= 0.0) || !isfinite(v)) return ORC_EINVAL;
+            }
+    }
     return 0;
 }
 
@@ -411,13 +505,16 @@ static int check_network(const orc_net *net, int d) {
  * (each may be NULL); final_states is [M][T][N][U] (may be NULL).
  */
 int orc_pf_loglik(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod,
-                  const int32_t *rate_index, const double *thetas, int64_t M, int32_t d,
-                  const int64_t *theta_ids, const int32_t *x0, const double *obs_times, int32_t K,
-                  const double *y, int32_t T, int32_t P, const double *Cm, const double *sigma,
-                  int32_t N, uint64_t seed, uint64_t budget, double *loglik, uint8_t *status,
-                  double *ll_traj, uint64_t *events, uint64_t *digest, int32_t *final_states) {
-    orc_net net = {U, R, reac, prod, rate_index};
-    if (check_network(&net, d)) return ORC_EINVAL;
+                  const int32_t *rate_index, const double *rate_coef, const double *thetas,
+                  int64_t M, int32_t d, const int64_t *theta_ids, const int32_t *x0,
+                  const int32_t *x0_hi, const double *obs_times, int32_t K, const double *y,
+                  int32_t T, int32_t P, const double *Cm, const double *sigma,
+                  const double *obs_offset, const double *obs_var, int32_t N, uint64_t seed,
+                  uint64_t budget, double *loglik, uint8_t *status, double *ll_traj,
+                  uint64_t *events, uint64_t *digest, int32_t *final_states) {
+    orc_net net = {U, R, reac, prod, rate_index, rate_coef, d};
+    orc_model mdl = {x0_hi, obs_offset, obs_var};
+    if (check_network(&net, d) || check_model(&mdl, x0, U, P)) return ORC_EINVAL;
     zig_init();
     if (N < 1 || N > 16384 || K < 1 || T < 1 || P < 1 || T >= 4096 || K >= (1 << 20))
         return ORC_EINVAL;
@@ -429,8 +526,8 @@ int orc_pf_loglik(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
         for (int traj = 0; traj < T; traj++) {
             filter_result fr;
             int32_t *fs = final_states ? &final_states[((size_t)mi * T + traj) * (size_t)N * U] : NULL;
-            int rc = run_filter(&net, theta, x0, obs_times, K, &y[(size_t)traj * K * P], P, Cm,
-                                sigma, N, seed, budget, (uint32_t)traj, m, &fr, fs);
+            int rc = run_filter(&net, &mdl, theta, x0, obs_times, K, &y[(size_t)traj * K * P], P,
+                                Cm, sigma, N, seed, budget, (uint32_t)traj, m, &fr, fs);
             if (rc) return rc;
             if (ll_traj) ll_traj[mi * T + traj] = fr.ll;
             if (events) events[mi * T + traj] = fr.events;
@@ -451,16 +548,19 @@ int orc_pf_loglik(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
  * states_out is [n_paths][K][U]; fired_out (may be NULL) is [n_paths].
  */
 int orc_ssa_paths(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod,
-                  const int32_t *rate_index, const double *theta, int32_t d, const int32_t *x0,
-                  const double *times, int32_t K, int64_t n_paths, uint64_t seed, uint64_t budget,
-                  int32_t *states_out, uint64_t *fired_out, uint8_t *status_out) {
-    orc_net net = {U, R, reac, prod, rate_index};
+                  const int32_t *rate_index, const double *rate_coef, const double *theta,
+                  int32_t d, const int32_t *x0, const double *times, int32_t K, int64_t n_paths,
+                  uint64_t seed, uint64_t budget, int32_t *states_out, uint64_t *fired_out,
+                  uint8_t *status_out) {
+    orc_net net = {U, R, reac, prod, rate_index, rate_coef, d};
     if (check_network(&net, d)) return ORC_EINVAL;
     zig_init();
     double *a = (double *)malloc(sizeof(double) * (size_t)R);
     double *S = (double *)malloc(sizeof(double) * (size_t)R);
+    double *rate = (double *)malloc(sizeof(double) * (size_t)R);
     int64_t *x = (int64_t *)malloc(sizeof(int64_t) * (size_t)U);
-    if (!a || !S || !x) { free(a); free(S); free(x); return ORC_ENOMEM; }
+    if (!a || !S || !x || !rate) { free(a); free(S); free(x); free(rate); return ORC_ENOMEM; }
+    reaction_rates(&net, theta, rate);
     for (int64_t i = 0; i < n_paths; i++) {
         for (int u = 0; u < U; u++) x[u] = x0[u];
         double t = 0.0;
@@ -468,7 +568,7 @@ int orc_ssa_paths(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
         int st = ORC_OK;
         for (int k = 0; k < K; k++) {
             if (st == ORC_OK)
-                st = ssa_advance(&net, theta, x, t, times[k], seed, (uint32_t)i, (uint32_t)k, 0u,
+                st = ssa_advance(&net, rate, x, t, times[k], seed, (uint32_t)i, (uint32_t)k, 0u,
                                  budget, a, S, &fired);
             t = times[k];
             for (int u = 0; u < U; u++) states_out[((size_t)i * K + k) * U + u] = (int32_t)x[u];
@@ -476,6 +576,6 @@ int orc_ssa_paths(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
         if (fired_out) fired_out[i] = fired;
         if (status_out) status_out[i] = (uint8_t)st;
     }
-    free(a); free(S); free(x);
+    free(a); free(S); free(x); free(rate);
     return 0;
 }

@@ -41,11 +41,11 @@ def _bind(path: Path) -> ct.CDLL:
     lib.orc_philox4x32_10.restype = None
     lib.orc_resample_systematic.argtypes = [P, ct.c_int32, ct.c_uint64, P]
     lib.orc_resample_systematic.restype = None
-    lib.orc_pf_loglik.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, ct.c_int64, ct.c_int32, P,
-                                  P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P, ct.c_int32,
-                                  ct.c_uint64, ct.c_uint64, P, P, P, P, P, P]
+    lib.orc_pf_loglik.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, P, ct.c_int64, ct.c_int32,
+                                  P, P, P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P, P, P,
+                                  ct.c_int32, ct.c_uint64, ct.c_uint64, P, P, P, P, P, P]
     lib.orc_pf_loglik.restype = ct.c_int
-    lib.orc_ssa_paths.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, ct.c_int32, P, P,
+    lib.orc_ssa_paths.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, P, ct.c_int32, P, P,
                                   ct.c_int32, ct.c_int64, ct.c_uint64, ct.c_uint64, P, P, P]
     lib.orc_ssa_paths.restype = ct.c_int
     lib.orc_exp_variates.argtypes = [ct.c_uint64, ct.c_int64, P]
@@ -119,11 +119,13 @@ class Oracle:
 
     def pf_loglik(self, net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, seed: int,
                       budget: int = DEFAULT_BUDGET, theta_ids=None,
-                      want_final_states: bool = False):
+                      want_final_states: bool = False, model: dict | None = None):
         """Filter log-likelihood of every theta row.
 
         net: {"reactants": [R][U], "products": [R][U], "rate_index": [R] or None}
-        y: [T][K][P].  Returns a dict with loglik[M], status[M], ll_traj[M][T],
+        y: [T][K][P].  model (optional): {"rate_coef": [R][d], "x0_hi": [U],
+        "obs_offset": [P], "obs_var": [P][U]}, any subset (the Lac-Gfp
+        extensions).  Returns a dict with loglik[M], status[M], ll_traj[M][T],
         events[M][T], digest[M][T] and optionally final_states[M][T][N][U].
         """
         lib = self._lib
@@ -144,6 +146,15 @@ class Oracle:
         Cm = _c(C, np.float64).reshape(P, U)
         sg = _c(sigma, np.float64).reshape(P)
         N = int(n_particles)
+        md = model or {}
+        rc_ = md.get("rate_coef")
+        rc_ = None if rc_ is None else _c(rc_, np.float64).reshape(R, d)
+        xhi = md.get("x0_hi")
+        xhi = None if xhi is None else _c(xhi, np.int32).reshape(U)
+        off = md.get("obs_offset")
+        off = None if off is None else _c(off, np.float64).reshape(P)
+        ov = md.get("obs_var")
+        ov = None if ov is None else _c(ov, np.float64).reshape(P, U)
         out = {
             "loglik": np.zeros(M, np.float64),
             "status": np.zeros(M, np.uint8),
@@ -152,8 +163,9 @@ class Oracle:
             "digest": np.zeros((M, T), np.uint64),
         }
         fs = np.zeros((M, T, N, U), np.int32) if want_final_states else None
-        rc = lib.orc_pf_loglik(U, R, _ptr(reac), _ptr(prod), _ptr(ri), _ptr(th), M, d, _ptr(ids),
-                               _ptr(x0), _ptr(ts), K, _ptr(yy), T, P, _ptr(Cm), _ptr(sg), N,
+        rc = lib.orc_pf_loglik(U, R, _ptr(reac), _ptr(prod), _ptr(ri), _ptr(rc_), _ptr(th), M, d,
+                               _ptr(ids), _ptr(x0), _ptr(xhi), _ptr(ts), K, _ptr(yy), T, P,
+                               _ptr(Cm), _ptr(sg), _ptr(off), _ptr(ov), N,
                                ct.c_uint64(int(seed)), ct.c_uint64(int(budget)),
                                _ptr(out["loglik"]), _ptr(out["status"]), _ptr(out["ll_traj"]),
                                _ptr(out["events"]), _ptr(out["digest"]), _ptr(fs))
@@ -165,8 +177,9 @@ class Oracle:
 
 
     def ssa_paths(self, net: dict, theta, x0, times, n_paths: int, seed: int,
-                      budget: int = DEFAULT_BUDGET):
-        """Independent direct-method paths; returns (states[n][K][U], fired[n], status[n])."""
+                      budget: int = DEFAULT_BUDGET, rate_coef=None):
+        """Independent direct-method paths; returns (states[n][K][U], fired[n], status[n]).
+        rate_coef [R][d] (optional) composes the rates from theta."""
         lib = self._lib
         reac = _c(net["reactants"], np.int32)
         prod = _c(net["products"], np.int32)
@@ -174,13 +187,15 @@ class Oracle:
         ri = net.get("rate_index")
         ri = None if ri is None else _c(ri, np.int32)
         th = _c(theta, np.float64).reshape(-1)
+        rcf = None if rate_coef is None else _c(rate_coef, np.float64).reshape(R, len(th))
         x0 = _c(x0, np.int32)
         ts = _c(times, np.float64)
         K = len(ts)
         states = np.zeros((n_paths, K, U), np.int32)
         fired = np.zeros(n_paths, np.uint64)
         status = np.zeros(n_paths, np.uint8)
-        rc = lib.orc_ssa_paths(U, R, _ptr(reac), _ptr(prod), _ptr(ri), _ptr(th), len(th), _ptr(x0),
+        rc = lib.orc_ssa_paths(U, R, _ptr(reac), _ptr(prod), _ptr(ri), _ptr(rcf), _ptr(th), len(th),
+                               _ptr(x0),
                                _ptr(ts), K, n_paths, ct.c_uint64(int(seed)), ct.c_uint64(int(budget)),
                                _ptr(states), _ptr(fired), _ptr(status))
         if rc != 0:

@@ -32,6 +32,17 @@ MUTANTS = {
     "philox_key_bump": ("k1 += 0xBB67AE85u;", "k1 += 0xBB67AE84u;", "philox"),
     "weights_before_resample_ignored": ("q[i] = (uint64_t)ldexp(exp(e[i] - emax), 32);",
                                         "q[i] = (uint64_t)1 << 32;", "unbiased"),
+    "initial_span_short": ("uint64_t span = (uint64_t)((int64_t)mdl->x0_hi[u] - x0[u] + 1);",
+                           "uint64_t span = (uint64_t)((int64_t)mdl->x0_hi[u] - x0[u]);",
+                           "init_uniform"),
+    "initial_same_word": ("v += (int64_t)(((uint64_t)w[u & 3] * span) >> 32);",
+                          "v += (int64_t)(((uint64_t)w[0] * span) >> 32);", "init_uniform"),
+    "state_variance_ignored": ("v = v + mdl->obs_var[p * U + u] * (double)x[(size_t)i * U + u];",
+                               "v = v;", "model_unbiased"),
+    "state_variance_log_dropped": ("lv = lv + log(v);", "lv = lv;", "model_unbiased"),
+    "composed_rate_transposed": ("v = v + net->rate_coef[r * net->d + c] * theta[c];",
+                                 "v = v + net->rate_coef[c * net->R + r] * theta[c];",
+                                 "model_unbiased"),
 }
 
 CHECKS = {
@@ -44,6 +55,8 @@ CHECKS = {
     "philox": lambda o, kat: pins.check_philox(o, kat),
     "unbiased": lambda o, kat: pins.check_unbiased(o, S=150, N=100),
     "exp_law": lambda o, kat: pins.check_exp_variates(o),
+    "init_uniform": lambda o, kat: pins.check_initial_uniform(o),
+    "model_unbiased": lambda o, kat: pins.check_model_unbiased(o, S=150, N=100),
 }
 
 

@@ -315,6 +315,111 @@ def test_filter_consistency_in_particle_count():
     assert err[2000] < 0.5 * err[200]
 
 
+# ------------------------------------ model extensions (Lac-Gfp forms) ----
+# Birth-death with k1 composed as theta_0 + 3 theta_1 and k2 = theta_2, the
+# initial count uniform on 5..15, and y ~ N(2 + 1.5 x, 1 + 0.5 x): the exact
+# forward algorithm handles each extension in its own plain form.
+MODEL = {"rate_coef": [[1.0, 3.0, 0.0], [0.0, 0.0, 1.0]], "x0_hi": [15], "obs_offset": [2.0],
+         "obs_var": [[0.5]]}
+
+
+def model_data():
+    w = W.birth_death()
+    xs, _, _ = orc().ssa_paths(BD, [10.0, 0.2], [9], w.obs_times, 1, seed=7070)
+    xk = xs[0, :, 0].astype(float)
+    rng = np.random.default_rng(77)
+    y = 2.0 + 1.5 * xk + rng.normal(size=len(xk)) * np.sqrt(1.0 + 0.5 * xk)
+    return w, y[None, :, None]
+
+
+def check_model_unbiased(o, S=300, N=200):
+    """E[p_hat] = p and Jensen for the extended model, against the exact
+    likelihood of the same model (composed rate, uniform x0, affine variance)."""
+    w, y = model_data()
+    for th, (k1, k2) in [([4.0, 2.0, 0.2], (10.0, 0.2)), ([8.0, 2.0, 0.3], (14.0, 0.3))]:
+        L, leak = exact_bd.loglik(k1, k2, 5, w.obs_times, y[0, :, 0], c=1.5, sigma=1.0, nmax=200,
+                                  x0_hi=15, obs_offset=2.0, obs_var=0.5)
+        assert abs(leak) < 1e-12
+        lls = np.array([o.pf_loglik(BD, [th], [5], w.obs_times, y, [[1.5]], [1.0], N, 6100 + s,
+                                    model=MODEL)["loglik"][0] for s in range(S)])
+        z = np.exp(lls - L)
+        se = z.std(ddof=1) / np.sqrt(S)
+        assert abs(z.mean() - 1.0) < 4 * se + 1e-3, (th, z.mean(), se)
+        assert lls.mean() <= L + 4 * lls.std(ddof=1) / np.sqrt(S)
+
+
+def test_extended_model_unbiased_against_exact():
+    check_model_unbiased(orc())
+
+
+def check_initial_uniform(o, n=16384):
+    """Initial particles of a random x0: each species uniform on its integers
+    lo..hi (chi-square), species independent (correlations), filters
+    (trajectories) independent.  Observation at t = 0: no simulation, so the
+    final states are the initial draws."""
+    net = W.cascade_network()
+    U = net["reactants"].shape[1]
+    R = net["reactants"].shape[0]
+    lo = np.arange(U, dtype=np.int32)
+    hi = lo + np.array([0, 1, 2, 3, 4, 5, 6, 7, 9, 30], np.int32)[:U]
+    T = 2
+    y = np.zeros((T, 1, 1))
+    C = np.zeros((1, U))
+    r = o.pf_loglik(net, np.ones((1, R)), lo, [0.0], y, C, [1.0], n, 31337,
+                    want_final_states=True, model={"x0_hi": hi})
+    fs = r["final_states"][0].astype(np.int64)            # [T][N][U]
+    for t in range(T):
+        X = fs[t]
+        for u in range(U):
+            span = int(hi[u] - lo[u] + 1)
+            assert X[:, u].min() >= lo[u] and X[:, u].max() <= hi[u]
+            if span == 1:
+                continue
+            cnt = np.bincount(X[:, u] - lo[u], minlength=span)
+            assert cnt.min() > 0
+            assert stats.chisquare(cnt).pvalue > 1e-4, (t, u, cnt)
+        Z = (X[:, 1:] - X[:, 1:].mean(0)) / X[:, 1:].std(0)
+        cor = (Z.T @ Z) / n - np.eye(U - 1)
+        assert np.abs(cor).max() < 5 / np.sqrt(n)
+    a = (fs[0, :, 9] - fs[0, :, 9].mean()) / fs[0, :, 9].std()
+    b = (fs[1, :, 9] - fs[1, :, 9].mean()) / fs[1, :, 9].std()
+    assert abs(np.mean(a * b)) < 5 / np.sqrt(n)
+
+
+def test_random_initial_state_uniform():
+    check_initial_uniform(orc())
+
+
+def test_extended_observation_reduces_to_basic():
+    """obs_var = 0 and obs_offset = 0 give the basic model's likelihood (the
+    log-weights differ by the constant sum_p log sigma_p moved out of the
+    normaliser, so values agree to rounding; resampling draws may differ only
+    through the 2^-20 grid of the quantised weights, which equal weights do
+    not feel: C = 0 makes all weights equal)."""
+    rng = np.random.default_rng(5)
+    y = rng.normal(size=(1, 6, 1)) * 2.0
+    base = orc().pf_loglik(GE, [[0.5, 0.2, 2.0, 0.1]], [3, 4], np.arange(1, 7) * 0.5, y,
+                           [[0.0, 0.0]], [1.3], 40, 8)
+    ext = orc().pf_loglik(GE, [[0.5, 0.2, 2.0, 0.1]], [3, 4], np.arange(1, 7) * 0.5, y,
+                          [[0.0, 0.0]], [1.3], 40, 8,
+                          model={"obs_var": [[0.0, 0.0]], "obs_offset": [0.0]})
+    assert np.isclose(base["loglik"][0], ext["loglik"][0], rtol=1e-13)
+    assert (base["digest"] == ext["digest"]).all()
+
+
+def test_composed_rates_reproduce_plain_rates():
+    """Composition with one unit coefficient per reaction is the plain rate
+    lookup, bit for bit (x + 0 and 1 * theta are exact)."""
+    w = W.gene_expression()
+    th = w.thetas(3)
+    rc = np.eye(4)
+    a = orc().pf_loglik(w.net, th, w.x0, w.obs_times[:5], w.observations()[:2, :5], w.C, w.sigma,
+                        30, 4)
+    b = orc().pf_loglik(w.net, th, w.x0, w.obs_times[:5], w.observations()[:2, :5], w.C, w.sigma,
+                        30, 4, model={"rate_coef": rc})
+    assert (a["loglik"] == b["loglik"]).all() and (a["digest"] == b["digest"]).all()
+
+
 # ------------------------------------------------------- bookkeeping ------
 def test_theta_ids_reproduce_batch_rows():
     w = W.birth_death()
