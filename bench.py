@@ -149,7 +149,7 @@ def _oracle_rows(args):
             break
         t0 = time.time()
         r = pf_oracle.pf_loglik(w.net, th[m:m + 1], w.x0, w.obs_times, y, w.C, w.sigma, w.N,
-                                w.filter_seed, theta_ids=[m])
+                                w.filter_seed, theta_ids=[m], model=w.model)
         dt = time.time() - t0
         if time.time() > deadline + 60:     # a row that overran far: not counted
             break
@@ -302,13 +302,16 @@ def main() -> None:
 
     def step():
         pf.pf_loglik(w.net, th, w.x0, w.obs_times, yd, w.C, w.sigma, w.N, w.filter_seed,
-                     out=out, stream=stream.cuda_stream, **launch)
+                     out=out, stream=stream.cuda_stream, model=w.model, **launch)
 
     for _ in range(a.warmup):
         step()
     torch.cuda.synchronize()
-    ev_step = int(out["events"].sum().item())
-    assert int((out["status"] != 0).sum().item()) == 0
+    ev_step = int(out["events"][out["status"] == 0].sum().item())   # finished rows' reactions
+    # rows may end with PF_ST_BUDGET (a prior draw whose reactions outrun the
+    # event budget: likelihood 0); nothing else may fail
+    budget_rows = int((out["status"] == pf.PF_ST_BUDGET).sum().item())
+    assert int(((out["status"] != 0) & (out["status"] != pf.PF_ST_BUDGET)).sum().item()) == 0
 
     # FP64 cost probe: FMA peak and the price of log / division
     probe = None if a.no_probe else fp64_probe(pf)
@@ -347,7 +350,7 @@ def main() -> None:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pf.pf_loglik(w.net, th_pin.numpy(), w.x0, w.obs_times, y_pin.numpy(), w.C, w.sigma, w.N,
-                     w.filter_seed, out=host_out)
+                     w.filter_seed, out=host_out, model=w.model)
         e2e_times.append(time.perf_counter() - t0)
     if e2e_times:
         assert np.array_equal(host_out["loglik"], out["loglik"].cpu().numpy())
@@ -371,7 +374,7 @@ def main() -> None:
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {**config_of(w), "launch": launch},
             "ssa_events_per_s": world * ev_step / (ms * 1e-3),
-            "events_per_step": ev_step,
+            "events_per_step": ev_step, "budget_rows": budget_rows,
             "clocks": clk,
             "e2e": {"value": world * M / e2e_s, "unit": "theta-likelihoods/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},

@@ -67,6 +67,7 @@ extern "C" {
 #define PF_MAX_REACTIONS 32
 #define PF_MAX_OBS_DIM 8
 #define PF_MAX_PARTICLES 16384
+#define PF_MAX_RATE_TERMS 4
 #define PF_DEFAULT_EVENT_BUDGET (1ull << 20)
 
 /*
@@ -127,8 +128,48 @@ typedef struct {
  *                 the threshold; which rows are rejected does not depend on
  *                 the launch (up to rounding of the running sum, ~1e-12
  *                 relative, for a row whose value equals the threshold).
+ *   model         optional model extensions (pf_model; NULL = the basic
+ *                 model: point-mass x0, rates theta[rate_index[r]], constant
+ *                 observation variance).
  *   Diagnostics are defined only for filters whose status is PF_ST_OK.
  */
+/*
+ * Model extensions of the paper's Lac-Gfp example (Supp. "LacGfp example");
+ * each field may be NULL (that part of the basic model then applies).  All
+ * HOST pointers, read during the call.
+ *   rate_coef   [R][d], entries >= 0 and finite, at most PF_MAX_RATE_TERMS
+ *               nonzero per row: reaction r's rate is
+ *                   sum_c rate_coef[r][c] * theta_c
+ *               summed over the nonzero entries in increasing c (composed
+ *               rates such as theta_4 + theta_5 [IPTG] with [IPTG] = 10);
+ *               replaces net->rate_index.
+ *   x0_hi       [U], x0_hi[u] >= x0[u]: each particle's initial count of
+ *               species u is uniform on the integers x0[u]..x0_hi[u] (the
+ *               paper's U([a, b]) initial distributions), drawn per
+ *               particle, species and filter from Philox word u & 3 of the
+ *               block with counter (particle, 0xFFFFFFFE,
+ *               (trajectory << 20) | (u >> 2), theta row) as
+ *               x0[u] + floor(word * (x0_hi[u] - x0[u] + 1) / 2^32).
+ *   obs_offset  [P] finite: the observation mean is obs_offset_p + (C x)_p.
+ *   obs_var     [P][U], entries >= 0 and finite: the observation variance
+ *               depends on the state, v_p = sigma_p^2 + sum_u obs_var[p][u] x_u
+ *               (fluorescence N(22.85 x, 5.72 sqrt(x)) is C = 22.85,
+ *               obs_var = 5.72^2 on the observed species; sigma_p and
+ *               obs_offset_p then describe a Gaussian background).  The
+ *               log-weight of a particle is -1/2 sum_p ((y_p - mu_p)^2 / v_p
+ *               + log v_p); the integer resampling weights are taken from
+ *               log-weights rounded to multiples of 2^-20 (so that the
+ *               last-place difference of two logarithm implementations cannot
+ *               shift every quantised weight), the likelihood from the
+ *               unrounded ones.
+ */
+typedef struct {
+    const double *rate_coef;
+    const int32_t *x0_hi;
+    const double *obs_offset;
+    const double *obs_var;
+} pf_model;
+
 #define PF_SCHED_AUTO 0
 #define PF_SCHED_NATURAL 1
 #define PF_SCHED_HEAVY_FIRST 2
@@ -145,6 +186,7 @@ typedef struct {
     int32_t early_reject;
     const uint32_t *row_order;
     double reject_below;
+    const pf_model *model;
 } pf_options;
 
 /*
@@ -246,6 +288,13 @@ int pf_ctx_create(pf_ctx **ctx, size_t mem_budget_bytes, int32_t n_slots, int32_
 int pf_ctx_load_problem(pf_ctx *ctx, const pf_network *net, int32_t d, const int32_t *x0,
                         const double *obs_times, int32_t K, const double *y, int32_t T,
                         int32_t P, const double *C, const double *sigma, int32_t *problem_id);
+
+/* pf_ctx_load_problem_model -- pf_ctx_load_problem with the model extensions
+ * of pf_model (may be NULL: the basic model). */
+int pf_ctx_load_problem_model(pf_ctx *ctx, const pf_network *net, int32_t d, const int32_t *x0,
+                              const double *obs_times, int32_t K, const double *y, int32_t T,
+                              int32_t P, const double *C, const double *sigma,
+                              const pf_model *model, int32_t *problem_id);
 
 /* One request: host arrays, read at submission (theta) and written at
  * completion (loglik/status; status may be NULL).  K_use = number of leading

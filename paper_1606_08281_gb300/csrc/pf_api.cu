@@ -48,21 +48,44 @@ void clear_error() { g_last_error.clear(); }
 
 // Build the kernels' network tables from the caller's description.
 int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P, const double *C,
-                 const double *sigma, pf::NetTables &t) {
+                 const double *sigma, const pf_model *model, pf::NetTables &t) {
     if (!net || !net->reactants || !net->products) return fail(PF_EINVAL, "network is NULL");
     const int U = net->n_species, R = net->n_reactions;
     if (U < 1 || U > PF_MAX_SPECIES) return fail(PF_EINVAL, "n_species %d outside 1..%d", U, PF_MAX_SPECIES);
     if (R < 1 || R > PF_MAX_REACTIONS) return fail(PF_EINVAL, "n_reactions %d outside 1..%d", R, PF_MAX_REACTIONS);
     if (P < 1 || P > PF_MAX_OBS_DIM) return fail(PF_EINVAL, "P %d outside 1..%d", P, PF_MAX_OBS_DIM);
     if (d < 1) return fail(PF_EINVAL, "d must be >= 1");
-    if (!net->rate_index && d < R) return fail(PF_EINVAL, "rate_index is NULL but d (%d) < R (%d)", d, R);
+    const double *rate_coef = model ? model->rate_coef : nullptr;
+    if (!rate_coef && !net->rate_index && d < R)
+        return fail(PF_EINVAL, "rate_index is NULL but d (%d) < R (%d)", d, R);
     if (!x0 || !C || !sigma) return fail(PF_EINVAL, "x0, C and sigma are required");
     memset(&t, 0, sizeof(t));
     t.U = U; t.R = R; t.P = P; t.d = d;
     for (int r = 0; r < R; ++r) {
-        const int col = net->rate_index ? net->rate_index[r] : r;
-        if (col < 0 || col >= d) return fail(PF_EINVAL, "rate_index[%d] = %d outside 0..%d", r, col, d - 1);
-        t.rate_col[r] = col;
+        if (rate_coef) {
+            // composed rate: the nonzero coefficients of row r, in column order
+            for (int c = 0; c < d; ++c) {
+                const double v = rate_coef[static_cast<size_t>(r) * d + c];
+                if (!(std::isfinite(v) && v >= 0.0))
+                    return fail(PF_EINVAL, "rate_coef[%d][%d] must be finite and >= 0", r, c);
+                if (v == 0.0) continue;
+                if (t.rate_nt[r] == PF_MAX_RATE_TERMS)
+                    return fail(PF_EINVAL, "rate_coef row %d has more than %d nonzero entries", r,
+                                PF_MAX_RATE_TERMS);
+                t.rate_tcol[r][t.rate_nt[r]] = (int8_t)c;
+                t.rate_tcoef[r][t.rate_nt[r]] = v;
+                t.rate_nt[r]++;
+            }
+            if (t.rate_nt[r] == 0) {  // an all-zero row: rate 0 (one zero term)
+                t.rate_tcol[r][0] = 0;
+                t.rate_tcoef[r][0] = 0.0;
+                t.rate_nt[r] = 1;
+            }
+        } else {
+            const int col = net->rate_index ? net->rate_index[r] : r;
+            if (col < 0 || col >= d) return fail(PF_EINVAL, "rate_index[%d] = %d outside 0..%d", r, col, d - 1);
+            t.rate_col[r] = col;
+        }
         t.sp_a[r] = t.sp_b[r] = -1;
         t.ord_a[r] = t.ord_b[r] = 0;
         int order = 0;
@@ -103,6 +126,13 @@ int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P,
     for (int u = 0; u < U; ++u) {
         if (x0[u] < 0) return fail(PF_EINVAL, "x0[%d] = %d < 0", u, x0[u]);
         t.x0[u] = x0[u];
+        t.x0_hi[u] = x0[u];
+        if (model && model->x0_hi) {
+            if (model->x0_hi[u] < x0[u])
+                return fail(PF_EINVAL, "x0_hi[%d] = %d < x0[%d] = %d", u, model->x0_hi[u], u, x0[u]);
+            t.x0_hi[u] = model->x0_hi[u];
+            if (t.x0_hi[u] > t.x0[u]) t.x0_random = 1;
+        }
     }
     for (int p = 0; p < P; ++p) {
         if (!(std::isfinite(sigma[p]) && sigma[p] > 0.0)) return fail(PF_EINVAL, "sigma[%d] must be finite and > 0", p);
@@ -110,6 +140,20 @@ int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P,
         for (int u = 0; u < U; ++u) {
             if (!std::isfinite(C[p * U + u])) return fail(PF_EINVAL, "C[%d][%d] is not finite", p, u);
             t.C[p][u] = C[p * U + u];
+        }
+        if (model && model->obs_offset) {
+            if (!std::isfinite(model->obs_offset[p]))
+                return fail(PF_EINVAL, "obs_offset[%d] is not finite", p);
+            t.obs_offset[p] = model->obs_offset[p];
+        }
+        if (model && model->obs_var) {
+            t.obs_state_var = 1;
+            for (int u = 0; u < U; ++u) {
+                const double v = model->obs_var[p * U + u];
+                if (!(std::isfinite(v) && v >= 0.0))
+                    return fail(PF_EINVAL, "obs_var[%d][%d] must be finite and >= 0", p, u);
+                t.obs_var[p][u] = v;
+            }
         }
     }
     return PF_OK;
@@ -120,7 +164,7 @@ int check_count_range(const pf::NetTables &t, int K, uint64_t budget) {
     int max_gain = 0, x0max = 0;
     for (int r = 0; r < t.R; ++r)
         for (int i = 0; i < t.n_change[r]; ++i) max_gain = std::max<int>(max_gain, t.ch_delta[r][i]);
-    for (int u = 0; u < t.U; ++u) x0max = std::max(x0max, t.x0[u]);
+    for (int u = 0; u < t.U; ++u) x0max = std::max(x0max, t.x0_hi[u]);
     const double worst = (double)x0max + (double)K * (double)budget * (double)max_gain;
     if (worst >= 2147483647.0)
         return fail(PF_EINVAL, "x0 + K * event_budget * max gain (%.3g) could overflow int32 counts; lower event_budget", worst);
@@ -195,7 +239,7 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     if (M > 0xFFFFFFFFll) return fail(PF_EINVAL, "M must be < 2^32");
     if (M * (int64_t)T > 0x7FFFFFFFll) return fail(PF_EINVAL, "M * T must be < 2^31");
     pf::FilterArgs a{};
-    int rc = build_tables(net, d, x0, P, C, sigma, a.net);
+    int rc = build_tables(net, d, x0, P, C, sigma, o.model, a.net);
     if (rc) return rc;
     rc = check_count_range(a.net, K, budget);
     if (rc) return rc;
@@ -395,7 +439,7 @@ extern "C" int pf_loglik_noalloc(const pf_network *net, const double *thetas, in
     if (!obs_times) return fail(PF_EINVAL, "obs_times is NULL");
     if (M > 0 && (!thetas || !y || !loglik)) return fail(PF_EINVAL, "NULL array argument");
     pf::FilterArgs a{};
-    int rc = build_tables(net, d, x0, P, C, sigma, a.net);
+    int rc = build_tables(net, d, x0, P, C, sigma, nullptr, a.net);
     if (rc) return rc;
     rc = check_count_range(a.net, K, budget);
     if (rc) return rc;

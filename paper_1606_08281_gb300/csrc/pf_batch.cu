@@ -632,13 +632,21 @@ int pf_ctx_create(pf_ctx **out, size_t mem_budget_bytes, int32_t n_slots, int32_
 int pf_ctx_load_problem(pf_ctx *ctx, const pf_network *net, int32_t d, const int32_t *x0,
                         const double *obs_times, int32_t K, const double *y, int32_t T,
                         int32_t P, const double *C, const double *sigma, int32_t *problem_id) {
+    return pf_ctx_load_problem_model(ctx, net, d, x0, obs_times, K, y, T, P, C, sigma, nullptr,
+                                     problem_id);
+}
+
+int pf_ctx_load_problem_model(pf_ctx *ctx, const pf_network *net, int32_t d, const int32_t *x0,
+                              const double *obs_times, int32_t K, const double *y, int32_t T,
+                              int32_t P, const double *C, const double *sigma,
+                              const pf_model *model, int32_t *problem_id) {
     pf::clear_error();
     if (!ctx || !problem_id) return fail(PF_EINVAL, "NULL argument");
     if (K < 1 || K >= (1 << 20)) return fail(PF_EINVAL, "K %d outside 1..2^20-1", K);
     if (T < 1 || T >= 4096) return fail(PF_EINVAL, "T %d outside 1..4095", T);
     if (!obs_times || !y) return fail(PF_EINVAL, "NULL array argument");
     ProblemHost p;
-    int rc = build_tables(net, d, x0, P, C, sigma, p.net);
+    int rc = build_tables(net, d, x0, P, C, sigma, model, p.net);
     if (rc) return rc;
     rc = pf::check_obs_times(obs_times, K);
     if (rc) return rc;

@@ -42,6 +42,7 @@ constexpr int kMaxRemnants = 128;  // >= block size
 constexpr int kParkLanes = 16;      // a warp below this many busy lanes parks its particles
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kResampleLane = 0xFFFFFFFFu;
+constexpr uint32_t kInitLane = 0xFFFFFFFEu;      // particle slot of the initial-state draws
 
 struct SharedHead {
     NetTables net;
@@ -92,6 +93,18 @@ struct Lane {
         }
     }
 };
+
+// Rate of reaction r for the theta row `theta`: theta[rate_col[r]], or a
+// composed rate, the sum of its nonzero terms coef * theta_c in column order
+// (equal to the sum over all columns, since adding +0 is exact).
+__device__ __forceinline__ double reaction_rate(const NetTables &n, const double *theta, int r) {
+    const int nt = n.rate_nt[r];
+    if (nt == 0) return theta[n.rate_col[r]];
+    double v = __dmul_rn(n.rate_tcoef[r][0], theta[n.rate_tcol[r][0]]);
+    for (int i = 1; i < nt; ++i)
+        v = __dadd_rn(v, __dmul_rn(n.rate_tcoef[r][i], theta[n.rate_tcol[r][i]]));
+    return v;
+}
 
 // h_r(x) = prod_u binom(x_u, p_ru)  (mass action, Sec. "Chemical Reaction Networks")
 template <int UM>
@@ -390,6 +403,11 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
     }
 }
 
+// e rounded to a multiple of 2^-20, ties to even (exact scalings by 2^20).
+__device__ __forceinline__ double grid20(double e) {
+    return __dmul_rn(rint(__dmul_rn(e, 1048576.0)), 1.0 / 1048576.0);
+}
+
 // Expected-work bucket of particle j for the interval (FP32, ordering only):
 // 15 - min(15, 1 + floor(log2(a0(x_j) * dt))), so heavy particles come first.
 __device__ __forceinline__ int cost_bucket(const SharedHead &sh, const int *xs, int Np, int j,
@@ -545,13 +563,17 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
         sh.valid = ok;
         sh.status = PF_ST_OK;
         sh.ll = 0.0;
+        // log of the Gaussian normalising constant; with a state-dependent
+        // variance the log v_p terms sit in each particle's log-weight instead
         double ln = 0.0;
-        for (int p = 0; p < P; ++p) ln = __dadd_rn(ln, log(sh.net.sigma[p]));
+        if (!sh.net.obs_state_var)
+            for (int p = 0; p < P; ++p) ln = __dadd_rn(ln, log(sh.net.sigma[p]));
         sh.lognorm = __dadd_rn(ln, __dmul_rn(0.5 * static_cast<double>(P), log(2.0 * M_PI)));
     }
     if (tid < R) {
-        sh.rate[tid] = theta[sh.net.rate_col[tid]];
-        sh.rate_f[tid] = static_cast<float>(theta[sh.net.rate_col[tid]]);
+        const double rt = reaction_rate(sh.net, theta, tid);
+        sh.rate[tid] = rt;
+        sh.rate_f[tid] = static_cast<float>(rt);
     }
     __syncthreads();
     if (!sh.valid) {
@@ -578,14 +600,37 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
     int *order = xs + U * Np;
     int *anc = order + N;
 
-    for (int j = tid; j < N; j += B)
-        for (int u = 0; u < U; ++u) xs[u * Np + j] = sh.net.x0[u];
-    __syncthreads();
-
     const uint32_t key0 = static_cast<uint32_t>(job.seed);
     const uint32_t key1 = static_cast<uint32_t>(job.seed >> 32);
     const uint32_t m32 = job.mrow;
     const int traj = job.traj;
+
+    // initial particles: x0, or each count uniform on x0..x0_hi (species
+    // group g = u >> 2 shares one Philox block; word u & 3)
+    for (int j = tid; j < N; j += B) {
+        if (sh.net.x0_random) {
+            for (int g = 0; g * 4 < U; ++g) {
+                const Philox4 w = philox4x32_10(static_cast<uint32_t>(j), kInitLane,
+                                                (static_cast<uint32_t>(traj) << 20) |
+                                                    static_cast<uint32_t>(g),
+                                                m32, key0, key1);
+                const uint32_t word[4] = {w.w0, w.w1, w.w2, w.w3};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int u = 4 * g + q;
+                    if (u < U) {
+                        const uint64_t span = static_cast<uint64_t>(
+                            static_cast<int64_t>(sh.net.x0_hi[u]) - sh.net.x0[u] + 1);
+                        xs[u * Np + j] = sh.net.x0[u] +
+                                         static_cast<int>((static_cast<uint64_t>(word[q]) * span) >> 32);
+                    }
+                }
+            }
+        } else {
+            for (int u = 0; u < U; ++u) xs[u * Np + j] = sh.net.x0[u];
+        }
+    }
+    __syncthreads();
     unsigned long long fired = 0, dig = 0;
     double t_prev = 0.0;
 
@@ -673,19 +718,32 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
                 dig += slot_digest(static_cast<uint32_t>(k), static_cast<uint32_t>(j),
                                    static_cast<uint32_t>(anc[j]), xs, Np, U);
 
-        // Gaussian log-weight exponent e_j = -1/2 sum_p ((y_p - (C x_j)_p) / sigma_p)^2
+        // Gaussian log-weight exponent e_j = -1/2 sum_p ((y_p - mu_p) / sigma_p)^2,
+        // mu_p = offset_p + (C x_j)_p; with a state-dependent variance
+        // v_p = sigma_p^2 + sum_u V_pu x_u, e_j = -1/2 sum_p ((y_p - mu_p)^2 / v_p + log v_p)
         const double *yk = job.y + static_cast<int64_t>(k) * P;
+        const bool svar = sh.net.obs_state_var != 0;
         double lmax = -INFINITY;
         for (int j = tid; j < N; j += B) {
-            double acc = 0.0;
+            double acc = 0.0, lv = 0.0;
             for (int p = 0; p < P; ++p) {
-                double mu = 0.0;
+                double mu = sh.net.obs_offset[p];
                 for (int u = 0; u < U; ++u)
                     mu = __dadd_rn(mu, __dmul_rn(sh.net.C[p][u], static_cast<double>(xs[u * Np + j])));
-                const double z = __ddiv_rn(__dsub_rn(yk[p], mu), sh.net.sigma[p]);
-                acc = __dadd_rn(acc, __dmul_rn(z, z));
+                if (svar) {
+                    double v = __dmul_rn(sh.net.sigma[p], sh.net.sigma[p]);
+                    for (int u = 0; u < U; ++u)
+                        v = __dadd_rn(v, __dmul_rn(sh.net.obs_var[p][u],
+                                                   static_cast<double>(xs[u * Np + j])));
+                    const double dv = __dsub_rn(yk[p], mu);
+                    acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(dv, dv), v));
+                    lv = __dadd_rn(lv, log(v));
+                } else {
+                    const double z = __ddiv_rn(__dsub_rn(yk[p], mu), sh.net.sigma[p]);
+                    acc = __dadd_rn(acc, __dmul_rn(z, z));
+                }
             }
-            const double e = __dmul_rn(-0.5, acc);
+            const double e = svar ? __dmul_rn(-0.5, __dadd_rn(acc, lv)) : __dmul_rn(-0.5, acc);
             wbuf[j] = e;
             lmax = fmax(lmax, e);
         }
@@ -696,11 +754,17 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
         }
         // p(y_k | y_<k) ~ (1/N) sum_j l_j  (Eq. likelihood approx.), in logs;
         // the same exp() values give the integer weights for the next resampling.
+        // With a state-dependent variance the integer weights come from the
+        // log-weights rounded to multiples of 2^-20 (grid20), the sum from the
+        // exact ones.
         double lsum = 0.0;
+        const double gmax = grid20(emax);
         for (int j = tid; j < N; j += B) {
-            const double v = exp(__dsub_rn(wbuf[j], emax));
+            const double e = wbuf[j];
+            const double v = exp(__dsub_rn(e, emax));
             lsum = __dadd_rn(lsum, v);
-            qbuf[j] = __double2ull_rz(__dmul_rn(v, 4294967296.0));
+            const double vq = svar ? exp(__dsub_rn(grid20(e), gmax)) : v;
+            qbuf[j] = __double2ull_rz(__dmul_rn(vq, 4294967296.0));
         }
         const double s = block_sum(lsum, sh);
         if (tid == 0) {

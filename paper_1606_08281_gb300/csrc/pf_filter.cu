@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(128) pilot_kernel(const FilterArgs args, uint3
     }
     double rate[RM];
 #pragma unroll
-    for (int r = 0; r < RM; ++r) rate[r] = r < R ? theta[net.rate_col[r]] : 0.0;
+    for (int r = 0; r < RM; ++r) rate[r] = r < R ? reaction_rate(net, theta, r) : 0.0;
     int x[PF_MAX_SPECIES];
     for (int u = 0; u < PF_MAX_SPECIES; ++u) x[u] = u < U ? net.x0[u] : 0;
     const uint32_t key0 = static_cast<uint32_t>(args.seed);

@@ -17,7 +17,10 @@ struct ZigTab;
 // their rate), i.e. what a particle taken from the pool computes first.
 struct NetTables {
     int32_t U, R, P, d;
-    int32_t rate_col[PF_MAX_REACTIONS];
+    int32_t rate_col[PF_MAX_REACTIONS];                  // rate_nt[r] == 0: theta[rate_col[r]]
+    int8_t rate_nt[PF_MAX_REACTIONS];                    // else sum of these terms, in order
+    int8_t rate_tcol[PF_MAX_REACTIONS][PF_MAX_RATE_TERMS];
+    double rate_tcoef[PF_MAX_REACTIONS][PF_MAX_RATE_TERMS];
     int8_t sp_a[PF_MAX_REACTIONS], ord_a[PF_MAX_REACTIONS];
     int8_t sp_b[PF_MAX_REACTIONS], ord_b[PF_MAX_REACTIONS];
     int8_t n_change[PF_MAX_REACTIONS];
@@ -29,8 +32,13 @@ struct NetTables {
     int8_t n_nz;                                         // reactions with reactants
     int8_t nz_list[PF_MAX_REACTIONS];                    // those reactions, ascending
     int32_t x0[PF_MAX_SPECIES];
+    int32_t x0_hi[PF_MAX_SPECIES];                       // == x0 unless the initial state is random
+    int32_t x0_random;                                   // some x0_hi[u] > x0[u]
+    int32_t obs_state_var;                               // obs_var given: state-dependent variance
     double C[PF_MAX_OBS_DIM][PF_MAX_SPECIES];
     double sigma[PF_MAX_OBS_DIM];
+    double obs_offset[PF_MAX_OBS_DIM];                   // 0 unless given
+    double obs_var[PF_MAX_OBS_DIM][PF_MAX_SPECIES];
 };
 
 // Arguments of one filter launch: F = M * T filters, filter f = m * T + traj.
@@ -99,7 +107,7 @@ int fail(int code, const char *fmt, ...);
 int cuda_fail(int cuda_error, const char *what);
 void clear_error();
 int build_tables(const pf_network *net, int32_t d, const int32_t *x0, int32_t P, const double *C,
-                 const double *sigma, NetTables &t);
+                 const double *sigma, const pf_model *model, NetTables &t);
 int check_count_range(const NetTables &t, int K, uint64_t budget);
 int check_obs_times(const double *obs_times, int K);
 

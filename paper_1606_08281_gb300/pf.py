@@ -29,7 +29,7 @@ PF_SCHED_AUTO, PF_SCHED_NATURAL, PF_SCHED_HEAVY_FIRST = 0, 1, 2
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",
             "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit", "pf_poll", "pf_ctx_stats",
-            "pf_ctx_destroy", "pf_exp_variates", "pf_div_check"]
+            "pf_ctx_destroy", "pf_exp_variates", "pf_div_check", "pf_ctx_load_problem_model"]
 
 
 class PfError(RuntimeError):
@@ -52,13 +52,41 @@ class pf_request(ct.Structure):
                 ("status", ct.c_void_p)]
 
 
+class pf_model(ct.Structure):
+    _fields_ = [("rate_coef", ct.c_void_p), ("x0_hi", ct.c_void_p), ("obs_offset", ct.c_void_p),
+                ("obs_var", ct.c_void_p)]
+
+
 class pf_options(ct.Structure):
     _fields_ = [("event_budget", ct.c_uint64), ("device_ptrs", ct.c_int32),
                 ("block_threads", ct.c_int32), ("stream", ct.c_void_p),
                 ("ll_traj", ct.c_void_p), ("events", ct.c_void_p), ("digest", ct.c_void_p),
                 ("final_states", ct.c_void_p), ("schedule", ct.c_int32),
                 ("early_reject", ct.c_int32), ("row_order", ct.c_void_p),
-                ("reject_below", ct.c_double)]
+                ("reject_below", ct.c_double), ("model", ct.POINTER(pf_model))]
+
+
+class _Model:
+    """pf_model from a dict {"rate_coef": [R][d], "x0_hi": [U], "obs_offset": [P],
+    "obs_var": [P][U]} (any subset); keeps the host arrays alive."""
+
+    def __init__(self, model: dict | None):
+        self.arrays = {}
+        self.s = None
+        if not model:
+            return
+        kinds = {"rate_coef": np.float64, "x0_hi": np.int32, "obs_offset": np.float64,
+                 "obs_var": np.float64}
+        unknown = set(model) - set(kinds)
+        if unknown:
+            raise ValueError(f"unknown model fields {sorted(unknown)}")
+        for k, dt in kinds.items():
+            if model.get(k) is not None:
+                self.arrays[k] = _host(model[k], dt)
+        self.s = pf_model(*[(_hptr(self.arrays[k]) if k in self.arrays else None) for k in kinds])
+
+    def ptr(self):
+        return None if self.s is None else ct.pointer(self.s)
 
 
 def library_path() -> Path:
@@ -105,6 +133,11 @@ def load():
             lib.pf_ctx_load_problem.argtypes = [V, ct.POINTER(pf_network), ct.c_int32, P, P,
                                                 ct.c_int32, P, ct.c_int32, ct.c_int32, P, P,
                                                 ct.POINTER(ct.c_int32)]
+            lib.pf_ctx_load_problem_model.argtypes = [V, ct.POINTER(pf_network), ct.c_int32, P,
+                                                      P, ct.c_int32, P, ct.c_int32, ct.c_int32,
+                                                      P, P, ct.POINTER(pf_model),
+                                                      ct.POINTER(ct.c_int32)]
+            lib.pf_ctx_load_problem_model.restype = ct.c_int
             lib.pf_ctx_run_batch.argtypes = [V, ct.POINTER(pf_request), ct.c_int32]
             lib.pf_submit.argtypes = [V, ct.POINTER(pf_request), ct.POINTER(ct.c_int64)]
             lib.pf_poll.argtypes = [V, ct.c_int64, ct.c_int32, ct.POINTER(ct.c_double),
@@ -164,8 +197,12 @@ def _is_torch_cuda(x) -> bool:
 def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, seed: int, *,
               event_budget: int = 0, block_threads: int = 0, stream=None,
               diagnostics: bool = False, final_states: bool = False, out=None,
-              schedule: int = PF_SCHED_AUTO, row_order=None, reject_below=None):
+              schedule: int = PF_SCHED_AUTO, row_order=None, reject_below=None,
+              model: dict | None = None):
     """Log-likelihood of every theta row (see pf_loglik in include/pf1606.h).
+
+    model: optional Lac-Gfp extensions {"rate_coef", "x0_hi", "obs_offset",
+    "obs_var"} (pf_model; host arrays).
 
     Returns a dict with 'loglik' [M] and 'status' [M]; with diagnostics=True
     also 'll_traj', 'events', 'digest' [M][T]; with final_states=True also
@@ -228,10 +265,11 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
     else:
         ro = _host(row_order, np.uint32)
         p_ro = _hptr(ro)
+    mdl = _Model(model)
     opt = pf_options(int(event_budget), 1 if device else 0, int(block_threads),
                      stream if device else None, ptr("ll_traj"), ptr("events"), ptr("digest"),
                      ptr("final_states"), int(schedule), 0 if reject_below is None else 1, p_ro,
-                     float("nan") if reject_below is None else float(reject_below))
+                     float("nan") if reject_below is None else float(reject_below), mdl.ptr())
     rc = lib.pf_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), p_ts, K, p_y, T, P, _hptr(Ch),
                        _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
                        ptr("loglik"), ptr("status"), ct.byref(opt))
@@ -321,18 +359,41 @@ def pf_ctx_create(mem_budget_bytes: int = 0, n_slots: int = 0, max_particles: in
     return h
 
 
-def pf_ctx_load_problem(ctx, net: dict, d: int, x0, obs_times, y, C, sigma) -> int:
+def pf_ctx_load_problem(ctx, net: dict, d: int, x0, obs_times, y, C, sigma,
+                        model: dict | None = None) -> int:
+    """Load a problem into a context; `model` as in pf_loglik (uses
+    pf_ctx_load_problem_model when given)."""
     lib = load()
     n = _Net(net)
     U = n.s.n_species
     yy = _host(y, np.float64)
     T, K, P = yy.shape
     pid = ct.c_int32()
-    _check(lib.pf_ctx_load_problem(ctx, ct.byref(n.s), int(d), _hptr(_host(x0, np.int32)),
-                                   _hptr(_host(obs_times, np.float64)), K, _hptr(yy), T, P,
-                                   _hptr(_host(C, np.float64).reshape(P, U)),
-                                   _hptr(_host(sigma, np.float64).reshape(P)), ct.byref(pid)),
-           "pf_ctx_load_problem")
+    args = (ctx, ct.byref(n.s), int(d), _hptr(_host(x0, np.int32)),
+            _hptr(_host(obs_times, np.float64)), K, _hptr(yy), T, P,
+            _hptr(_host(C, np.float64).reshape(P, U)), _hptr(_host(sigma, np.float64).reshape(P)))
+    if model:
+        return pf_ctx_load_problem_model(ctx, net, d, x0, obs_times, y, C, sigma, model)
+    _check(lib.pf_ctx_load_problem(*args, ct.byref(pid)), "pf_ctx_load_problem")
+    return pid.value
+
+
+def pf_ctx_load_problem_model(ctx, net: dict, d: int, x0, obs_times, y, C, sigma,
+                              model: dict | None) -> int:
+    """pf_ctx_load_problem with the pf_model extensions (None: the basic model)."""
+    lib = load()
+    n = _Net(net)
+    U = n.s.n_species
+    yy = _host(y, np.float64)
+    T, K, P = yy.shape
+    pid = ct.c_int32()
+    mdl = _Model(model)
+    _check(lib.pf_ctx_load_problem_model(ctx, ct.byref(n.s), int(d), _hptr(_host(x0, np.int32)),
+                                         _hptr(_host(obs_times, np.float64)), K, _hptr(yy), T, P,
+                                         _hptr(_host(C, np.float64).reshape(P, U)),
+                                         _hptr(_host(sigma, np.float64).reshape(P)), mdl.ptr(),
+                                         ct.byref(pid)),
+           "pf_ctx_load_problem_model")
     return pid.value
 
 

@@ -115,6 +115,55 @@ def cascade_network(seed: int = 3000, U: int = 10, n0: int = 4, n1: int = 10, n2
     }
 
 
+LAC_GFP_SPECIES = ["lacI", "LACI", "LACI2", "PLac", "O2Lac", "O4Lac", "gfp", "GFP", "mGFP"]
+IPTG_uM = 10.0
+
+
+def lac_gfp_network() -> dict:
+    """The Lac-Gfp network of Supp. "LacGfp example": 9 species, 18 mass-action
+    reactions, 18 parameters.  Reaction 4 (LACI degradation) has the composed
+    rate theta_4 + theta_5 [IPTG] with [IPTG] = 10 uM; reaction 18 (mGFP
+    degradation) shares theta_17 with reaction 16 (GFP degradation).  The
+    rates are given by `rate_coef` [R][d] (pf_model)."""
+    ix = {s: i for i, s in enumerate(LAC_GFP_SPECIES)}
+    rx = [({}, {"lacI": 1}),                                    # 1  theta_1
+          ({"lacI": 1}, {}),                                    # 2  theta_2
+          ({"lacI": 1}, {"lacI": 1, "LACI": 1}),                # 3  theta_3
+          ({"LACI": 1}, {}),                                    # 4  theta_4 + theta_5 [IPTG]
+          ({"LACI": 2}, {"LACI2": 1}),                          # 5  theta_6
+          ({"LACI2": 1}, {"LACI": 2}),                          # 6  theta_7
+          ({"LACI2": 1, "PLac": 1}, {"O2Lac": 1}),              # 7  theta_8
+          ({"O2Lac": 1}, {"LACI2": 1, "PLac": 1}),              # 8  theta_9
+          ({"O2Lac": 2}, {"O4Lac": 1}),                         # 9  theta_10
+          ({"O4Lac": 1}, {"O2Lac": 2}),                         # 10 theta_11
+          ({"PLac": 1}, {"PLac": 1, "gfp": 1}),                 # 11 theta_12
+          ({"O2Lac": 1}, {"O2Lac": 1, "gfp": 1}),               # 12 theta_13
+          ({"O4Lac": 1}, {"O4Lac": 1, "gfp": 1}),               # 13 theta_14
+          ({"gfp": 1}, {}),                                     # 14 theta_15
+          ({"gfp": 1}, {"gfp": 1, "GFP": 1}),                   # 15 theta_16
+          ({"GFP": 1}, {}),                                     # 16 theta_17
+          ({"GFP": 1}, {"mGFP": 1}),                            # 17 theta_18
+          ({"mGFP": 1}, {})]                                    # 18 theta_17
+    R, U = len(rx), len(LAC_GFP_SPECIES)
+    reac = np.zeros((R, U), np.int32)
+    prod = np.zeros((R, U), np.int32)
+    for r, (a, b) in enumerate(rx):
+        for k, v in a.items():
+            reac[r, ix[k]] = v
+        for k, v in b.items():
+            prod[r, ix[k]] = v
+    cols = [0, 1, 2, None, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 16]
+    rate_coef = np.zeros((R, 18))
+    for r, c in enumerate(cols):
+        if c is None:
+            rate_coef[r, 3] = 1.0
+            rate_coef[r, 4] = IPTG_uM
+        else:
+            rate_coef[r, c] = 1.0
+    return {"name": "lac_gfp", "species": LAC_GFP_SPECIES, "reactants": reac, "products": prod,
+            "rate_index": None, "rate_coef": rate_coef}
+
+
 # --------------------------------------------------------------------------
 # parameter draws
 # --------------------------------------------------------------------------
@@ -146,6 +195,7 @@ class Workload:
     filter_seed: int
     data_seed: int
     y: np.ndarray | None = field(default=None)   # float64 [T][K][P]
+    model: dict | None = field(default=None)     # pf_model extensions (None: basic model)
 
     @property
     def U(self) -> int:
@@ -217,7 +267,41 @@ def cascade() -> Workload:
         data_seed=3001, theta_seed=3002, filter_seed=3003)
 
 
-WORKLOADS = {"birth_death": birth_death, "gene_expression": gene_expression, "cascade": cascade}
+# Lac-Gfp (Supp. "LacGfp example"): theta* and the log-uniform prior of the
+# paper's table; theta_10's prior is printed as [0.16, 1.600] beside
+# theta_10* = 173.576 and is read as [0.16, 1600].  Observation of mGFP:
+# N(22.85 x, 5.72 sqrt(x)) plus a background; the paper's measured background
+# distribution is not available, so a Gaussian N(100, 30^2) stands in.
+LAC_GFP_THETA_STAR = np.array([1.215, 7.430, 1.439, 3.971, 1.173, 1716.683, 6.282, 0.433, 0.679,
+                               173.576, 0.623, 119.232, 0.120, 0.006, 1.673, 32.318, 1.196,
+                               2.102])
+LAC_GFP_PRIOR = np.array([[1, 50], [0.1, 30], [1, 50], [0.1, 20], [1, 100], [0.16, 3000],
+                          [0.1, 20], [0.0016, 1.6], [0.1, 20], [0.16, 1600], [0.1, 20], [1, 150],
+                          [0.1, 15], [1e-5, 1], [0.1, 20], [1, 50], [0.1, 20], [0.1, 20]], float)
+LAC_GFP_X0_LO = np.array([0, 0, 0, 0, 0, 50, 0, 0, 0], np.int32)
+LAC_GFP_X0_HI = np.array([5, 10, 0, 0, 0, 70, 0, 0, 0], np.int32)
+LAC_GFP_GAIN, LAC_GFP_NOISE = 22.85, 5.72
+LAC_GFP_BACKGROUND = (100.0, 30.0)
+
+
+def lac_gfp() -> Workload:
+    net = lac_gfp_network()
+    C = np.zeros((1, 9))
+    C[0, 8] = LAC_GFP_GAIN
+    V = np.zeros((1, 9))
+    V[0, 8] = LAC_GFP_NOISE ** 2
+    model = {"rate_coef": net["rate_coef"], "x0_hi": LAC_GFP_X0_HI,
+             "obs_offset": np.array([LAC_GFP_BACKGROUND[0]]), "obs_var": V}
+    return Workload(
+        name="lac_gfp", net=net, x0=LAC_GFP_X0_LO.copy(),
+        obs_times=np.arange(1, 30, dtype=np.float64), C=C,
+        sigma=np.array([LAC_GFP_BACKGROUND[1]]), prior_lo=LAC_GFP_PRIOR[:, 0],
+        prior_hi=LAC_GFP_PRIOR[:, 1], theta_star=LAC_GFP_THETA_STAR.copy(), T=4, M=256, N=200,
+        data_seed=6001, theta_seed=6002, filter_seed=6003, model=model)
+
+
+WORKLOADS = {"birth_death": birth_death, "gene_expression": gene_expression, "cascade": cascade,
+             "lac_gfp": lac_gfp}
 
 
 def get(name: str) -> Workload:

@@ -24,6 +24,8 @@ from paper_1606_08281_gb300 import workloads  # noqa: E402
 
 
 def simulate(w: workloads.Workload) -> dict:
+    if w.model is not None:
+        return simulate_model(w)
     states, fired, status = pf_oracle.ssa_paths(w.net, w.theta_star, w.x0, w.obs_times, w.T,
                                                 seed=w.data_seed)
     assert (status == 0).all()
@@ -39,6 +41,42 @@ def simulate(w: workloads.Workload) -> dict:
         "events": fired.tolist(),
         "data_seed": w.data_seed,
         "noise_seed": w.data_seed + 100,
+    }
+
+
+def simulate_model(w: workloads.Workload) -> dict:
+    """Workloads with the Lac-Gfp extensions: each trajectory starts from its
+    own draw of the uniform initial distribution, rates are composed, and the
+    observation is y = offset + C x + sqrt(sigma^2 + V x) * N(0, 1)."""
+    md = w.model
+    x0_rng = np.random.default_rng(w.data_seed + 200)
+    noise_rng = np.random.default_rng(w.data_seed + 100)
+    lo, hi = w.x0, np.asarray(md["x0_hi"], np.int32)
+    all_states, all_fired, x0s = [], [], []
+    for traj in range(w.T):
+        x0 = x0_rng.integers(lo, hi + 1).astype(np.int32)
+        states, fired, status = pf_oracle.ssa_paths(w.net, w.theta_star, x0, w.obs_times, 1,
+                                                    seed=w.data_seed + traj,
+                                                    rate_coef=md["rate_coef"])
+        assert (status == 0).all()
+        all_states.append(states[0])
+        all_fired.append(int(fired[0]))
+        x0s.append(x0.tolist())
+    states = np.array(all_states)                                   # [T][K][U]
+    xs = states.astype(np.float64)
+    mean = np.asarray(md["obs_offset"])[None, None, :] + np.einsum("pu,tku->tkp", w.C, xs)
+    var = (w.sigma ** 2)[None, None, :] + np.einsum("pu,tku->tkp", np.asarray(md["obs_var"]), xs)
+    y = mean + noise_rng.normal(size=mean.shape) * np.sqrt(var)
+    return {
+        "y": y.tolist(),
+        "x_true": states.tolist(),
+        "theta_star": w.theta_star.tolist(),
+        "x0": x0s,
+        "obs_times": w.obs_times.tolist(),
+        "events": all_fired,
+        "data_seed": w.data_seed,
+        "noise_seed": w.data_seed + 100,
+        "x0_seed": w.data_seed + 200,
     }
 
 
