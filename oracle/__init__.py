@@ -11,4 +11,8 @@ no code with the CUDA library in ``paper_1606_08281_gb300``.
 * ``oracle.exact_bd``: exact likelihood of the birth-death network by the
   forward algorithm on a truncated state space (the verification route the
   paper names, FSP, Supp. "posterior verification").
+* ``oracle.fsp``: the same forward algorithm for any network on a box of
+  counts (finite state projection of the chemical master equation), with
+  scipy's sparse matrix-exponential action as the propagation step; the
+  reference for the CUDA FSP kernel.
 """

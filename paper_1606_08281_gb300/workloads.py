@@ -55,6 +55,19 @@ def gene_expression_network() -> dict:
     }
 
 
+def telegraph_network() -> dict:
+    """The RNA model of Supp. "Verification of approximated posterior":
+    G_off -> G_on (theta_1), G_on -> G_off (theta_2), G_on -> G_on + RNA
+    (theta_3), RNA -> 0 (theta_4)."""
+    return {
+        "name": "telegraph",
+        "species": ["G_on", "G_off", "RNA"],
+        "reactants": np.array([[0, 1, 0], [1, 0, 0], [1, 0, 0], [0, 0, 1]], np.int32),
+        "products": np.array([[1, 0, 0], [0, 1, 0], [1, 0, 1], [0, 0, 0]], np.int32),
+        "rate_index": None,
+    }
+
+
 def cascade_network(seed: int = 3000, U: int = 10, n0: int = 4, n1: int = 10, n2: int = 6) -> dict:
     """Seeded synthetic signalling cascade with mass-action orders <= 2.
 
@@ -196,6 +209,7 @@ class Workload:
     data_seed: int
     y: np.ndarray | None = field(default=None)   # float64 [T][K][P]
     model: dict | None = field(default=None)     # pf_model extensions (None: basic model)
+    fsp_box: np.ndarray | None = field(default=None)  # int32 [U] box of the exact (FSP) likelihood
 
     @property
     def U(self) -> int:
@@ -241,7 +255,7 @@ def birth_death() -> Workload:
         obs_times=np.arange(1, 21, dtype=np.float64), C=np.array([[1.0]]),
         sigma=np.array([1.0]), prior_lo=np.array([1.0, 0.05]), prior_hi=np.array([50.0, 1.0]),
         theta_star=np.array([10.0, 0.2]), T=1, M=200, N=100,
-        data_seed=1001, theta_seed=1002, filter_seed=1003)
+        data_seed=1001, theta_seed=1002, filter_seed=1003, fsp_box=np.array([1200], np.int32))
 
 
 def gene_expression() -> Workload:
@@ -300,8 +314,27 @@ def lac_gfp() -> Workload:
         data_seed=6001, theta_seed=6002, filter_seed=6003, model=model)
 
 
+def telegraph() -> Workload:
+    """The paper's RNA model: one trajectory of mRNA observed at 25 equally
+    spaced times in (0, 200], theta_1 unknown (log-uniform prior
+    [1e-6, 0.006]), theta_2..4 known.  The observation noise is not stated;
+    read as RNA + N(0, 1).  Data seed 7003 is the first from 7001 on whose path
+    switches the gene on within the 200 time units (theta_1* = 0.001 leaves the
+    gene off in most paths, and then the data carry little information)."""
+    ts = np.array([0.001, 0.002, 0.06, 0.002])
+    lo = ts.copy()
+    hi = ts.copy()
+    lo[0], hi[0] = 1e-6, 0.006
+    return Workload(
+        name="telegraph", net=telegraph_network(), x0=np.array([0, 1, 0], np.int32),
+        obs_times=8.0 * np.arange(1, 26, dtype=np.float64), C=np.array([[0.0, 0.0, 1.0]]),
+        sigma=np.array([1.0]), prior_lo=lo, prior_hi=hi, theta_star=ts, T=1, M=4096, N=200,
+        data_seed=7003, theta_seed=7101, filter_seed=7102,
+        fsp_box=np.array([1, 1, 60], np.int32))
+
+
 WORKLOADS = {"birth_death": birth_death, "gene_expression": gene_expression, "cascade": cascade,
-             "lac_gfp": lac_gfp}
+             "lac_gfp": lac_gfp, "telegraph": telegraph}
 
 
 def get(name: str) -> Workload:
