@@ -259,10 +259,12 @@ def main() -> None:
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--probe-only", action="store_true",
                     help="run the FP64 cost probe alone and print it")
-    ap.add_argument("--mode", default="step", choices=["step", "hetero", "serve"],
+    ap.add_argument("--mode", default="step", choices=["step", "hetero", "serve", "fsp"],
                     help="step: the contract's timed step; hetero: one batch of a "
                          "heterogeneous request mix vs plain per-request launches; serve: a "
-                         "Poisson request stream, continuous batching vs a plain FIFO server")
+                         "Poisson request stream, continuous batching vs a plain FIFO server; "
+                         "fsp: the exact FSP likelihood of a workload with an FSP box "
+                         "(telegraph, birth_death)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--autotune", action="store_true",
@@ -289,6 +291,9 @@ def main() -> None:
     pf.load()
     if a.probe_only:
         print(json.dumps(fp64_probe(pf)), flush=True)
+        return
+    if a.mode == "fsp":
+        run_fsp(a, pf)
         return
     if a.mode != "step":
         run_pattern(a)
@@ -437,6 +442,89 @@ def run_pattern(a) -> None:
                                        "gene_expression (theta 4-512, N 256, K 10) and cascade "
                                        "(theta 1-32, N 128, K 5), coin-flipped"},
                 **res}
+    print(json.dumps(line), flush=True)
+
+
+def fsp_ops(w, th) -> float:
+    """Algorithmic FP64 operations of the FSP uniformization for theta rows th:
+    per row, lambda = max over the box of a_0(x); per interval, nsub sub-steps
+    of jmax stencil products; each product costs R + 2 fused multiply-adds per
+    state (R inflows from the predecessors, the diagonal term, the weighted
+    sum of the series)."""
+    box = np.asarray(w.fsp_box, np.int64)
+    grids = np.meshgrid(*[np.arange(n + 1) for n in box], indexing="ij")
+    X = np.stack([g.reshape(-1) for g in grids], axis=1)
+    reac = np.asarray(w.net["reactants"], np.int64)
+    h = np.ones((X.shape[0], reac.shape[0]))
+    for r in range(reac.shape[0]):
+        for u in range(reac.shape[1]):
+            if reac[r, u] == 1:
+                h[:, r] *= X[:, u]
+            elif reac[r, u] == 2:
+                h[:, r] *= X[:, u] * (X[:, u] - 1) / 2
+    R, S = reac.shape[0], X.shape[0]
+    dts = np.diff(np.concatenate([[0.0], w.obs_times]))
+    total = 0.0
+    for row in th:
+        lam = float((h * row[:R][None, :]).sum(axis=1).max())
+        for dt in dts:
+            if dt <= 0 or lam <= 0:
+                continue
+            nsub = int(np.ceil(lam * dt / 1500.0))
+            lh = lam * dt / nsub
+            jmax = min(2047, int(np.ceil(lh + 8.5 * np.sqrt(lh) + 20.0)))
+            total += nsub * jmax * S * (R + 2)
+    return total
+
+
+def run_fsp(a, pf) -> None:
+    """The exact FSP likelihood of every theta row of a workload (one JSON line)."""
+    import torch
+    w = W.get(a.workload if a.workload in ("telegraph", "birth_death") else "telegraph")
+    th_np = w.thetas()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    th = torch.from_numpy(th_np).to(dev)
+    yd = torch.from_numpy(w.observations()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        return pf.pf_fsp_loglik(w.net, th, w.x0, w.fsp_box, w.obs_times, yd, w.C, w.sigma,
+                                model=w.model, stream=stream.cuda_stream)
+
+    for _ in range(max(3, a.warmup)):
+        r = step()
+    torch.cuda.synchronize()
+    assert int((r["status"] != 0).sum().item()) == 0
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    ms = float(np.mean(times))
+    ops = fsp_ops(w, th_np)
+    ops_rate = ops / (ms * 1e-3)
+    peak_ops = FP64_PEAK_TFLOPS * 1e12 / 2.0          # one FP64 operation per lane per slot
+    line = {"metric": "exact FSP theta-likelihoods/s", "mode": "fsp", "value": w.M / (ms * 1e-3),
+            "unit": "theta-likelihoods/s", "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"{w.name}: FSP box {list(map(int, w.fsp_box))}, "
+                                   f"K={w.K} T={w.T} M={w.M}",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": ops_rate / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T FP64 ops/s", "frac": ops_rate / peak_ops, "traffic": None,
+                         "kernel": "fsp_kernel (FP64 pipe; the probability vectors stay in "
+                                   "shared memory)",
+                         "fp64_ops_per_step": ops}}
     print(json.dumps(line), flush=True)
 
 

@@ -216,6 +216,43 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
               uint64_t seed, double *loglik, uint8_t *status, const pf_options *opt);
 
 /*
+ * pf_fsp_loglik -- the exact (truncated) log-likelihood of M theta rows by
+ * the finite state projection of the chemical master equation, the route the
+ * paper uses to verify its sampler (Supp. "Verification of approximated
+ * posterior": the RNA model's "(almost) exact" likelihood).  On the box
+ * {x : 0 <= x_u <= box_max[u]} probability flows by the network's reactions;
+ * a jump that would leave the box is dropped (its mass is the leak), so the
+ * value is a lower bound that becomes exact as the box grows.  With the same
+ * observation model as pf_loglik (Gaussian y_k given C x, or the pf_model
+ * extensions) the likelihood factorises over observation times like the
+ * filter's estimate, and each factor p(y_k | y_<k) is computed exactly:
+ * propagate the state distribution over the interval (uniformization: a
+ * Poisson-weighted series of substochastic stencil products, truncated below
+ * 1e-17), weight by p(y_k | x), normalise.  The particle filter is an
+ * unbiased estimator of exp of this value.
+ *   Arguments as in pf_loglik, plus box_max [U] (host), the box; the product
+ *   of (box_max[u] + 1) must be <= PF_FSP_MAX_STATES (the whole probability
+ *   vector stays in shared memory).  x0 (and x0_hi of the model) must lie in
+ *   the box.  There are no particles and no random numbers.
+ *   loglik [M] out: sum over the T trajectories of the per-trajectory values;
+ *   status [M] out (may be NULL): PF_ST_OK, PF_ST_INVALID_THETA, or
+ *   PF_ST_NONFINITE when an observation has zero probability on the box.
+ * Returns PF_OK or a negative code.
+ */
+#define PF_FSP_MAX_STATES 8192
+typedef struct {
+    int32_t device_ptrs;   /* 1: thetas, y, loglik, status, ll_traj, leak are device pointers */
+    void *stream;          /* cudaStream_t (NULL = legacy default stream) */
+    double *ll_traj;       /* optional [M][T] per-trajectory values */
+    double *leak;          /* optional [M][T] probability mass that left the box */
+    const pf_model *model; /* optional model extensions */
+} pf_fsp_options;
+int pf_fsp_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
+                  const int32_t *x0, const int32_t *box_max, const double *obs_times, int32_t K,
+                  const double *y, int32_t T, int32_t P, const double *C, const double *sigma,
+                  double *loglik, uint8_t *status, const pf_fsp_options *opt);
+
+/*
  * pf_loglik_noalloc -- pf_loglik for callers that must not allocate device
  * memory.  The paper has no counterpart: this is an integration entry point.
  * Some callers cannot call cudaMalloc: a process whose device memory is

@@ -139,7 +139,7 @@ def loglik(net: dict, theta, x0, box_max, obs_times, y_traj, C, sigma, model: di
         alpha = np.maximum(alpha, 0.0)                 # expm_multiply rounding near zero
         leak += mass_in - alpha.sum()
         le = log_emission(y_traj[k], X, C, sigma, md)
-        m = le.max()
+        m = le[alpha > 0].max() if (alpha > 0).any() else le.max()   # shift on the support
         w = alpha * np.exp(le - m)
         c = w.sum()
         L += m + np.log(c)

@@ -29,7 +29,8 @@ PF_SCHED_AUTO, PF_SCHED_NATURAL, PF_SCHED_HEAVY_FIRST = 0, 1, 2
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",
             "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit", "pf_poll", "pf_ctx_stats",
-            "pf_ctx_destroy", "pf_exp_variates", "pf_div_check", "pf_ctx_load_problem_model"]
+            "pf_ctx_destroy", "pf_exp_variates", "pf_div_check", "pf_ctx_load_problem_model",
+            "pf_fsp_loglik"]
 
 
 class PfError(RuntimeError):
@@ -64,6 +65,11 @@ class pf_options(ct.Structure):
                 ("final_states", ct.c_void_p), ("schedule", ct.c_int32),
                 ("early_reject", ct.c_int32), ("row_order", ct.c_void_p),
                 ("reject_below", ct.c_double), ("model", ct.POINTER(pf_model))]
+
+
+class pf_fsp_options(ct.Structure):
+    _fields_ = [("device_ptrs", ct.c_int32), ("stream", ct.c_void_p), ("ll_traj", ct.c_void_p),
+                ("leak", ct.c_void_p), ("model", ct.POINTER(pf_model))]
 
 
 class _Model:
@@ -138,6 +144,10 @@ def load():
                                                       P, P, ct.POINTER(pf_model),
                                                       ct.POINTER(ct.c_int32)]
             lib.pf_ctx_load_problem_model.restype = ct.c_int
+            lib.pf_fsp_loglik.argtypes = [ct.POINTER(pf_network), P, ct.c_int64, ct.c_int32, P, P,
+                                          P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P, P, P,
+                                          ct.POINTER(pf_fsp_options)]
+            lib.pf_fsp_loglik.restype = ct.c_int
             lib.pf_ctx_run_batch.argtypes = [V, ct.POINTER(pf_request), ct.c_int32]
             lib.pf_submit.argtypes = [V, ct.POINTER(pf_request), ct.POINTER(ct.c_int64)]
             lib.pf_poll.argtypes = [V, ct.c_int64, ct.c_int32, ct.POINTER(ct.c_double),
@@ -274,6 +284,61 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
                        _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
                        ptr("loglik"), ptr("status"), ct.byref(opt))
     _check(rc, "pf_loglik")
+    return out
+
+
+def pf_fsp_loglik(net: dict, thetas, x0, box_max, obs_times, y, C, sigma, *,
+                  model: dict | None = None, diagnostics: bool = False, stream=None, out=None):
+    """Exact (truncated) log-likelihood by the finite state projection (see
+    pf_fsp_loglik in include/pf1606.h).  Returns 'loglik' [M], 'status' [M] and,
+    with diagnostics=True, 'll_traj' and 'leak' [M][T]; numpy arrays (host
+    mode) or torch CUDA tensors (device mode, when `thetas` is one)."""
+    lib = load()
+    n = _Net(net)
+    U = n.s.n_species
+    x0h = _host(x0, np.int32)
+    box = _host(box_max, np.int32).reshape(U)
+    device = _is_torch_cuda(thetas)
+    if device:
+        import torch
+        th = thetas.contiguous()
+        M, d = th.shape
+        yy = y.contiguous()
+        T, K, P = yy.shape
+        dev = th.device
+        if out is None:
+            out = {"loglik": torch.empty(M, dtype=torch.float64, device=dev),
+                   "status": torch.empty(M, dtype=torch.uint8, device=dev)}
+            if diagnostics:
+                out["ll_traj"] = torch.empty((M, T), dtype=torch.float64, device=dev)
+                out["leak"] = torch.empty((M, T), dtype=torch.float64, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        ptr = lambda k: (out[k].data_ptr() if k in out else None)  # noqa: E731
+        p_th, p_y = th.data_ptr(), yy.data_ptr()
+    else:
+        th = _host(thetas, np.float64)
+        if th.ndim == 1:
+            th = th[None, :]
+        M, d = th.shape
+        yy = _host(y, np.float64)
+        T, K, P = yy.shape
+        if out is None:
+            out = {"loglik": np.empty(M, np.float64), "status": np.empty(M, np.uint8)}
+            if diagnostics:
+                out["ll_traj"] = np.empty((M, T), np.float64)
+                out["leak"] = np.empty((M, T), np.float64)
+        ptr = lambda k: (out[k].ctypes.data if k in out else None)  # noqa: E731
+        p_th, p_y = _hptr(th), _hptr(yy)
+    ts = _host(obs_times, np.float64)
+    mdl = _Model(model)
+    opt = pf_fsp_options(1 if device else 0, stream if device else None, ptr("ll_traj"),
+                         ptr("leak"), mdl.ptr())
+    rc = lib.pf_fsp_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), _hptr(box), _hptr(ts), K, p_y, T,
+                           P, _hptr(_host(C, np.float64).reshape(P, U)),
+                           _hptr(_host(sigma, np.float64).reshape(P)), ptr("loglik"),
+                           ptr("status"), ct.byref(opt))
+    _check(rc, "pf_fsp_loglik")
     return out
 
 
