@@ -15,4 +15,7 @@ no code with the CUDA library in ``paper_1606_08281_gb300``.
   counts (finite state projection of the chemical master equation), with
   scipy's sparse matrix-exponential action as the propagation step; the
   reference for the CUDA FSP kernel.
+* ``oracle.ode``: the deterministic likelihood of the Egf-Ras-Raf-Mek-Erk
+  model (its reaction equations and FRET noise model) with scipy's
+  Dormand-Prince integrator; the reference for the CUDA ODE kernel.
 """

@@ -337,6 +337,89 @@ WORKLOADS = {"birth_death": birth_death, "gene_expression": gene_expression, "ca
              "lac_gfp": lac_gfp, "telegraph": telegraph}
 
 
+# --------------------------------------------------------------------------
+# the deterministic Egf-Ras-Raf-Mek-Erk model (ODE likelihood)
+# --------------------------------------------------------------------------
+# theta layout (36): 27 kinetic constants (k1, gamma1, k2, K2, gamma2, D2, k3,
+# K3, K_NFB, gamma3, D3, k4, K4, gamma4, D4, k5, K5, gamma5, D5, k6, K6, K6R,
+# gamma6, D6, dusp_basal, dusp_ind, K_dusp), the initial EGFR, NFB and
+# dusp (= DUSP) concentrations, and the FRET model (bg, lam, sigma, E, f_AA,
+# f_DD).  Priors as in the paper's tables: kinetic constants log-uniform on
+# [e^-10, e^5], initial concentrations [e^-8, e^1], FRET bg and lam
+# [e^-7, e^6], sigma [e^-8, e^-3], E [e^-4, e^-0.5], f_AA and f_DD [e^-8, e^5].
+ERK_PRIOR_LO = np.exp(np.array([-10.0] * 27 + [-8.0] * 3 + [-7.0, -7.0, -8.0, -4.0, -8.0, -8.0]))
+ERK_PRIOR_HI = np.exp(np.array([5.0] * 27 + [1.0] * 3 + [6.0, 6.0, -3.0, -0.5, 5.0, 5.0]))
+# The data-generating parameters are not in the paper (its data are measured);
+# this synthetic theta gives a FRET response of about 0.5 -> 0.8 with a slow
+# Dusp feedback over two hours.
+ERK_THETA_BAR = np.array([1.0, 0.1, 1.0, 0.5, 0.5, 0.5, 1.0, 0.5, 0.5, 0.5, 0.5, 1.0, 0.5, 0.5,
+                          0.5, 1.0, 0.5, 5.0, 0.5, 0.5, 0.5, 0.5, 0.1, 0.5, 0.001, 100.0, 0.01,
+                          1.0, 0.5, 0.001, 0.5, 1.0, 0.02, 0.3, 1.0, 1.0])
+
+
+def _pulses(period: float, width: float, end: float = 120.0):
+    st, sv, t = [], [], 0.0
+    while t < end:
+        st += [t, t + width]
+        sv += [1.0, 0.0]
+        t += period
+    return np.array(st), np.array(sv)
+
+
+def erk_patterns() -> list:
+    """Six EGF input patterns (the paper's stimuli are not given): a sustained
+    step, one 10-min pulse, 5-min pulses every 20 and every 40 min, 3-min pulses
+    every 10 min, and two 20-min pulses an hour apart.  Each is (switch times,
+    values): the input is values[i] from switch time i on."""
+    return [(np.array([0.0]), np.array([1.0])), (np.array([0.0, 10.0]), np.array([1.0, 0.0])),
+            _pulses(20.0, 5.0), _pulses(40.0, 5.0), _pulses(10.0, 3.0),
+            (np.array([0.0, 20.0, 60.0, 80.0]), np.array([1.0, 0.0, 1.0, 0.0]))]
+
+
+@dataclass
+class ErkWorkload:
+    name: str = "erk"
+    theta_bar: np.ndarray = field(default_factory=lambda: ERK_THETA_BAR.copy())
+    prior_lo: np.ndarray = field(default_factory=lambda: ERK_PRIOR_LO.copy())
+    prior_hi: np.ndarray = field(default_factory=lambda: ERK_PRIOR_HI.copy())
+    obs_times: np.ndarray = field(default_factory=lambda: 2.0 * np.arange(1, 61))
+    M: int = 4096
+    theta_seed: int = 8002
+    data_seed: int = 8001
+    y: np.ndarray | None = None
+
+    @property
+    def patterns(self) -> list:
+        return erk_patterns()
+
+    @property
+    def K(self) -> int:
+        return int(len(self.obs_times))
+
+    def thetas(self, M: int | None = None, spread: float = 1.0) -> np.ndarray:
+        """Log-uniform draws within a factor e^spread of theta_bar (clipped to
+        the prior): a neighbourhood such as the sampler's later level sets."""
+        lo = np.maximum(self.prior_lo, self.theta_bar * np.exp(-spread))
+        hi = np.minimum(self.prior_hi, self.theta_bar * np.exp(spread))
+        rng = np.random.default_rng(self.theta_seed)
+        full = log_uniform(rng, lo, hi, self.M)
+        return np.ascontiguousarray(full[: (self.M if M is None else M)])
+
+    def prior_thetas(self, M: int, seed: int = 8003) -> np.ndarray:
+        return log_uniform(np.random.default_rng(seed), self.prior_lo, self.prior_hi, M)
+
+    def observations(self) -> np.ndarray:
+        """[n_patterns][K] FRET observations."""
+        if self.y is None:
+            with open(OBSERVATIONS_PATH) as f:
+                self.y = np.array(json.load(f)["erk"]["y"], dtype=np.float64)
+        return self.y
+
+
+def erk() -> ErkWorkload:
+    return ErkWorkload()
+
+
 def get(name: str) -> Workload:
     return WORKLOADS[name]()
 

@@ -80,12 +80,25 @@ def simulate_model(w: workloads.Workload) -> dict:
     }
 
 
+def simulate_erk(w) -> dict:
+    """The Erk ODE model at theta_bar for each input pattern, plus
+    N(0, sigma^2) measurement noise (sigma = theta_bar[32])."""
+    from oracle import ode
+    mean = ode.observe(w.theta_bar, w.patterns, w.obs_times)
+    rng = np.random.default_rng(w.data_seed)
+    y = mean + rng.normal(size=mean.shape) * w.theta_bar[32]
+    return {"y": y.tolist(), "mean": mean.tolist(), "theta_bar": w.theta_bar.tolist(),
+            "obs_times": w.obs_times.tolist(), "data_seed": w.data_seed}
+
+
 def main() -> None:
     out = {}
     for name, make in workloads.WORKLOADS.items():
         w = make()
         out[name] = simulate(w)
         print(name, "events per path:", out[name]["events"][:4], "...")
+    out["erk"] = simulate_erk(workloads.erk())
+    print("erk: FRET range", min(map(min, out["erk"]["y"])), max(map(max, out["erk"]["y"])))
     with open(workloads.OBSERVATIONS_PATH, "w") as f:
         json.dump(out, f, indent=None, separators=(",", ":"))
         f.write("\n")
