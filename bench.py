@@ -259,12 +259,12 @@ def main() -> None:
     ap.add_argument("--no-probe", action="store_true")
     ap.add_argument("--probe-only", action="store_true",
                     help="run the FP64 cost probe alone and print it")
-    ap.add_argument("--mode", default="step", choices=["step", "hetero", "serve", "fsp"],
+    ap.add_argument("--mode", default="step", choices=["step", "hetero", "serve", "fsp", "ode"],
                     help="step: the contract's timed step; hetero: one batch of a "
                          "heterogeneous request mix vs plain per-request launches; serve: a "
                          "Poisson request stream, continuous batching vs a plain FIFO server; "
                          "fsp: the exact FSP likelihood of a workload with an FSP box "
-                         "(telegraph, birth_death)")
+                         "(telegraph, birth_death); ode: the deterministic Erk-model likelihood")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--autotune", action="store_true",
@@ -294,6 +294,9 @@ def main() -> None:
         return
     if a.mode == "fsp":
         run_fsp(a, pf)
+        return
+    if a.mode == "ode":
+        run_ode(a, pf)
         return
     if a.mode != "step":
         run_pattern(a)
@@ -525,6 +528,66 @@ def run_fsp(a, pf) -> None:
                          "kernel": "fsp_kernel (FP64 pipe; the probability vectors stay in "
                                    "shared memory)",
                          "fp64_ops_per_step": ops}}
+    print(json.dumps(line), flush=True)
+
+
+# FP64 operations of one Dormand-Prince step of the Erk model: six new
+# right-hand sides (per evaluation 56 multiplies/adds and 13 IEEE divisions at
+# 8 operations each = 160), the stage combinations (stage s takes s - 1
+# multiply-adds for the weighted sum and one for x + h (...): 2 + ... + 7 = 27
+# per component) and the error estimate (6 multiply-adds, the step factor,
+# the scale, one division and the square: ~20 per component).
+ODE_OPS_PER_STEP = 6 * 160 + 14 * 27 + 14 * 20
+
+
+def run_ode(a, pf) -> None:
+    """The Erk-model likelihood of every theta row (one JSON line)."""
+    import torch
+    w = W.erk()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    th = torch.from_numpy(w.thetas()).to(dev)
+    yd = torch.from_numpy(w.observations()).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    out = None
+
+    def step():
+        return pf.pf_erk_loglik(th, w.patterns, w.obs_times, yd, diagnostics=True,
+                                stream=stream.cuda_stream, out=out)
+
+    for _ in range(max(3, a.warmup)):
+        out = step()
+    torch.cuda.synchronize()
+    assert int((out["status"] != 0).sum().item()) == 0
+    steps = int(out["steps"].to(torch.int64).sum().item())
+    clocks = ClockSampler(dev.index)
+    clocks.start()
+    times = []
+    for _ in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    ms = float(np.mean(times))
+    ops_rate = steps * ODE_OPS_PER_STEP / (ms * 1e-3)
+    peak_ops = FP64_PEAK_TFLOPS * 1e12 / 2.0
+    line = {"metric": "ODE theta-likelihoods/s", "mode": "ode", "value": w.M / (ms * 1e-3),
+            "unit": "theta-likelihoods/s", "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
+            "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"erk: {w.M} theta (within a factor e of theta_bar) x "
+                                   f"{len(w.patterns)} input patterns x {w.K} FRET readings",
+                       "rtol": 1e-10, "atol": 1e-13,
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "dp_steps_per_launch": steps, "clocks": clk,
+            "roofline": {"bound": "alu", "achieved": ops_rate / 1e12, "peak": peak_ops / 1e12,
+                         "unit": "T FP64 ops/s", "frac": ops_rate / peak_ops, "traffic": None,
+                         "kernel": "erk_kernel (FP64 pipe; one thread per theta and pattern)",
+                         "fp64_ops_per_dp_step": ODE_OPS_PER_STEP}}
     print(json.dumps(line), flush=True)
 
 

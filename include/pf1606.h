@@ -253,6 +253,51 @@ int pf_fsp_loglik(const pf_network *net, const double *thetas, int64_t M, int32_
                   double *loglik, uint8_t *status, const pf_fsp_options *opt);
 
 /*
+ * pf_erk_loglik -- the deterministic likelihood of the paper's
+ * Egf-Ras-Raf-Mek-Erk model (Supp. "Egf-Ras-Raf-Mek-Erk model": the reaction
+ * equations, the species table and the FRET noise model; Sec. "A realistic
+ * example": a deterministic model needs no particle filter -- solve the ODE
+ * and score the trajectory).  For each theta row and each input pattern the
+ * 14 concentrations (EGFR, EGFR*, Ras, Ras*, Raf, Raf*, MEK, MEK*, ERK,
+ * ERK*, NFB, NFB*, dusp, DUSP) are integrated from t = 0 by an adaptive
+ * Dormand-Prince 5(4) method (error per step below atol + rtol |x| in the
+ * root-mean-square norm), stepping onto every input switch and observation
+ * time, and the value is
+ *     sum_patterns sum_k log N(y[p][k]; R(x(t_k)), sigma^2),
+ *     R = lam (ERK* E f_AA / ((ERK + (1 - E) ERK*) f_DD) + bg).
+ *   thetas   [M][36], all > 0 and E < 1 (else PF_ST_INVALID_THETA): k1,
+ *            gamma1, k2, K2, gamma2, D2, k3, K3, K_NFB, gamma3, D3, k4, K4,
+ *            gamma4, D4, k5, K5, gamma5, D5, k6, K6, K6R, gamma6, D6,
+ *            dusp_basal, dusp_ind, K_dusp, EGFR(0), NFB(0), dusp(0) =
+ *            DUSP(0), bg, lam, sigma, E, f_AA, f_DD.  Fixed: Ras(0) = 0.1,
+ *            Raf(0) = 0.7, MEK(0) = 0.68, ERK(0) = 0.26, active forms 0,
+ *            T_dusp = T_DUSP = 90 min with the factor log10(2)/T as printed.
+ *   switch_times / switch_values / switch_offsets (host): pattern p's EGF
+ *            input is switch_values[i] from switch_times[i] on, for i in
+ *            switch_offsets[p] .. switch_offsets[p+1]-1 (increasing times;
+ *            0 before the first switch).
+ *   obs_times [K] (host), strictly increasing, obs_times[0] > 0.
+ *   y        [n_patterns][K] observations.
+ *   loglik   [M] out; status [M] out (may be NULL): PF_ST_OK, INVALID_THETA,
+ *            BUDGET (more than max_steps steps for some pattern: a stiff or
+ *            diverging theta; loglik -inf), NONFINITE.
+ * Returns PF_OK or a negative code.
+ */
+#define PF_ERK_N_THETA 36
+typedef struct {
+    int32_t device_ptrs;   /* 1: thetas, y, loglik, status, ll_pattern, steps are device pointers */
+    void *stream;          /* cudaStream_t (NULL = legacy default stream) */
+    double rtol, atol;     /* 0 = defaults 1e-10, 1e-13 */
+    int32_t max_steps;     /* per pattern (accepted + rejected); 0 = default 200000 */
+    double *ll_pattern;    /* optional [M][n_patterns] per-pattern values */
+    uint32_t *steps;       /* optional [M][n_patterns] steps taken */
+} pf_ode_options;
+int pf_erk_loglik(const double *thetas, int64_t M, const double *switch_times,
+                  const double *switch_values, const int32_t *switch_offsets, int32_t n_patterns,
+                  const double *obs_times, int32_t K, const double *y, double *loglik,
+                  uint8_t *status, const pf_ode_options *opt);
+
+/*
  * pf_loglik_noalloc -- pf_loglik for callers that must not allocate device
  * memory.  The paper has no counterpart: this is an integration entry point.
  * Some callers cannot call cudaMalloc: a process whose device memory is

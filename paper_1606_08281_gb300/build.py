@@ -19,7 +19,7 @@ CSRC = PKG / "csrc"
 BUILD = PKG / "_build"
 LIB = BUILD / "libpf1606.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["pf_filter.cu", "pf_api.cu", "pf_probe.cu", "pf_batch.cu", "pf_fsp.cu"]
+SOURCES = ["pf_filter.cu", "pf_api.cu", "pf_probe.cu", "pf_batch.cu", "pf_fsp.cu", "pf_ode.cu"]
 
 
 def nvcc() -> str:

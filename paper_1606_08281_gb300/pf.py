@@ -30,7 +30,7 @@ EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philo
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",
             "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit", "pf_poll", "pf_ctx_stats",
             "pf_ctx_destroy", "pf_exp_variates", "pf_div_check", "pf_ctx_load_problem_model",
-            "pf_fsp_loglik"]
+            "pf_fsp_loglik", "pf_erk_loglik"]
 
 
 class PfError(RuntimeError):
@@ -70,6 +70,12 @@ class pf_options(ct.Structure):
 class pf_fsp_options(ct.Structure):
     _fields_ = [("device_ptrs", ct.c_int32), ("stream", ct.c_void_p), ("ll_traj", ct.c_void_p),
                 ("leak", ct.c_void_p), ("model", ct.POINTER(pf_model))]
+
+
+class pf_ode_options(ct.Structure):
+    _fields_ = [("device_ptrs", ct.c_int32), ("stream", ct.c_void_p), ("rtol", ct.c_double),
+                ("atol", ct.c_double), ("max_steps", ct.c_int32), ("ll_pattern", ct.c_void_p),
+                ("steps", ct.c_void_p)]
 
 
 class _Model:
@@ -148,6 +154,9 @@ def load():
                                           P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P, P, P,
                                           ct.POINTER(pf_fsp_options)]
             lib.pf_fsp_loglik.restype = ct.c_int
+            lib.pf_erk_loglik.argtypes = [P, ct.c_int64, P, P, P, ct.c_int32, P, ct.c_int32, P, P,
+                                          P, ct.POINTER(pf_ode_options)]
+            lib.pf_erk_loglik.restype = ct.c_int
             lib.pf_ctx_run_batch.argtypes = [V, ct.POINTER(pf_request), ct.c_int32]
             lib.pf_submit.argtypes = [V, ct.POINTER(pf_request), ct.POINTER(ct.c_int64)]
             lib.pf_poll.argtypes = [V, ct.c_int64, ct.c_int32, ct.POINTER(ct.c_double),
@@ -339,6 +348,61 @@ def pf_fsp_loglik(net: dict, thetas, x0, box_max, obs_times, y, C, sigma, *,
                            _hptr(_host(sigma, np.float64).reshape(P)), ptr("loglik"),
                            ptr("status"), ct.byref(opt))
     _check(rc, "pf_fsp_loglik")
+    return out
+
+
+def pf_erk_loglik(thetas, patterns, obs_times, y, *, rtol: float = 0.0, atol: float = 0.0,
+                  max_steps: int = 0, diagnostics: bool = False, stream=None, out=None):
+    """Deterministic likelihood of the Egf-Ras-Raf-Mek-Erk model (see
+    pf_erk_loglik in include/pf1606.h).  patterns: list of (switch_times,
+    switch_values) per input pattern; y [n_patterns][K].  Returns 'loglik' [M],
+    'status' [M] and, with diagnostics=True, 'll_pattern' and 'steps'
+    [M][n_patterns]; numpy (host mode) or torch CUDA tensors (device mode)."""
+    lib = load()
+    st = np.concatenate([np.asarray(t, np.float64) for t, _ in patterns])
+    sv = np.concatenate([np.asarray(v, np.float64) for _, v in patterns])
+    off = np.zeros(len(patterns) + 1, np.int32)
+    off[1:] = np.cumsum([len(t) for t, _ in patterns])
+    NP = len(patterns)
+    ts = _host(obs_times, np.float64)
+    K = len(ts)
+    device = _is_torch_cuda(thetas)
+    if device:
+        import torch
+        th = thetas.contiguous()
+        M = th.shape[0]
+        yy = y.contiguous()
+        dev = th.device
+        if out is None:
+            out = {"loglik": torch.empty(M, dtype=torch.float64, device=dev),
+                   "status": torch.empty(M, dtype=torch.uint8, device=dev)}
+            if diagnostics:
+                out["ll_pattern"] = torch.empty((M, NP), dtype=torch.float64, device=dev)
+                out["steps"] = torch.empty((M, NP), dtype=torch.int32, device=dev)
+        if stream is None:
+            stream = torch.cuda.current_stream(dev).cuda_stream
+        ptr = lambda k: (out[k].data_ptr() if k in out else None)  # noqa: E731
+        p_th, p_y = th.data_ptr(), yy.data_ptr()
+    else:
+        th = _host(thetas, np.float64)
+        if th.ndim == 1:
+            th = th[None, :]
+        M = th.shape[0]
+        yy = _host(y, np.float64).reshape(NP, K)
+        if out is None:
+            out = {"loglik": np.empty(M, np.float64), "status": np.empty(M, np.uint8)}
+            if diagnostics:
+                out["ll_pattern"] = np.empty((M, NP), np.float64)
+                out["steps"] = np.empty((M, NP), np.uint32)
+        ptr = lambda k: (out[k].ctypes.data if k in out else None)  # noqa: E731
+        p_th, p_y = _hptr(th), _hptr(yy)
+    if th.shape[-1] != 36:
+        raise ValueError("thetas must have 36 columns")
+    opt = pf_ode_options(1 if device else 0, stream if device else None, float(rtol), float(atol),
+                         int(max_steps), ptr("ll_pattern"), ptr("steps"))
+    rc = lib.pf_erk_loglik(p_th, M, _hptr(st), _hptr(sv), _hptr(off), NP, _hptr(ts), K, p_y,
+                           ptr("loglik"), ptr("status"), ct.byref(opt))
+    _check(rc, "pf_erk_loglik")
     return out
 
 
