@@ -225,7 +225,8 @@ __global__ void __launch_bounds__(kFspMaxThreads) fsp_kernel(const FspArgs a) {
                             double out = diag[i] * cur[i];
                             for (int r = 0; r < R; ++r) {
                                 const double c = cin[r * S + i];
-                                const int src = c != 0.0 ? i - a.off[r] : i;   // in range either way
+                                // c >= +0: its bits are nonzero iff c != 0 (an integer test)
+                                const int src = __double_as_longlong(c) != 0 ? i - a.off[r] : i;
                                 out = fma(c, cur[src], out);
                             }
                             nxt[i] = out;

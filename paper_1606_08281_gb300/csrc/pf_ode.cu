@@ -91,10 +91,13 @@ constexpr double E1 = 71.0 / 57600.0, E3 = -71.0 / 16695.0, E4 = 71.0 / 1920.0,
                  E5 = -17253.0 / 339200.0, E6 = 22.0 / 525.0, E7 = -1.0 / 40.0;
 
 __global__ void __launch_bounds__(kThreads) erk_kernel(const OdeArgs a) {
-    const int64_t f = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (f >= a.M * a.NP) return;
-    const int64_t m = f / a.NP;
-    const int p = static_cast<int>(f - m * a.NP);
+    // threads run pattern-major (g = p * M + m): the lanes of a warp share an
+    // input pattern, so they stop at the same switch times and diverge less
+    const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (g >= a.M * a.NP) return;
+    const int p = static_cast<int>(g / a.M);
+    const int64_t m = g - static_cast<int64_t>(p) * a.M;
+    const int64_t f = m * a.NP + p;                 // result slot [m][p]
     double th[36];
     bool ok = true;
     for (int i = 0; i < 36; ++i) {
