@@ -490,11 +490,12 @@ int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n);
 int pf_exp_variates(uint64_t seed, int64_t n, double *out);
 
 /*
- * pf_div_check -- test support for the SSA waiting time tau = E / a0: over n
- * pseudo-random (E, a0) pairs, counts the quotients where the kernels'
- * division (reciprocal seed, one Newton step, residual-corrected quotient)
- * differs from the IEEE quotient.  Synchronous.  PF_OK, PF_EINVAL, PF_ENOMEM
- * or PF_ECUDA.
+ * pf_div_check -- test support for the kernels' divisions: over n
+ * pseudo-random pairs, counts the quotients where the SSA waiting time's
+ * division tau = E / a0 (reciprocal seed, one Newton step, residual-corrected
+ * quotient) or the Gaussian weight's division by sigma (rounded reciprocal
+ * computed once, residual-corrected quotient; signed numerators) differs from
+ * the IEEE quotient.  Synchronous.  PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.
  */
 int pf_div_check(uint64_t seed, int64_t n, uint64_t *mismatches);
 

@@ -264,6 +264,9 @@ struct Slot {
     std::vector<int64_t> ids;   // requests in flight on this slot
     bool busy = false;
     std::atomic<bool> finished{false};
+    // argument of the completion callback: (context, slot index); a slot has at
+    // most one batch in flight, so it stays valid until that callback has run
+    std::pair<pf_ctx *, int> cb_arg{nullptr, 0};
 };
 
 struct pf_ctx {
@@ -296,8 +299,6 @@ void CUDART_CB slot_done_callback(void *p) {
     ctx->slots[pair->second].finished.store(true);
     ctx->cv.notify_all();
 }
-std::pair<pf_ctx *, int> g_cb_args[kMaxSlots * 64];
-std::atomic<int> g_cb_next{0};
 
 void free_slot(Slot &s) {
     if (s.exec) cudaGraphExecDestroy(s.exec);
@@ -504,9 +505,8 @@ int launch_batch(pf_ctx *ctx, int si, const std::vector<ReqState *> &batch) {
     cudaError_t e = cudaGraphLaunch(s.exec, s.stream);
     if (e == cudaSuccess) e = cudaEventRecord(s.done, s.stream);
     if (e == cudaSuccess) {
-        const int ci = g_cb_next.fetch_add(1) % (kMaxSlots * 64);
-        g_cb_args[ci] = {ctx, si};
-        e = cudaLaunchHostFunc(s.stream, slot_done_callback, &g_cb_args[ci]);
+        s.cb_arg = {ctx, si};
+        e = cudaLaunchHostFunc(s.stream, slot_done_callback, &s.cb_arg);
     }
     ctx->n_batches++;
     ctx->n_filters += filters;

@@ -62,6 +62,7 @@ struct SharedHead {
     double rem_t[2][kMaxRemnants];       // its time
     int bucket[16];
     float rate_f[PF_MAX_REACTIONS];  // FP32 copy of rate[], for cost estimates only
+    double inv_sigma[PF_MAX_OBS_DIM];  // 1 / sigma_p, correctly rounded
     ZigX zig;                 // ziggurat layer edges
     const ZigTab *zig_g;      // the full ziggurat table (global memory)
 };
@@ -569,6 +570,7 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
         if (!sh.net.obs_state_var)
             for (int p = 0; p < P; ++p) ln = __dadd_rn(ln, log(sh.net.sigma[p]));
         sh.lognorm = __dadd_rn(ln, __dmul_rn(0.5 * static_cast<double>(P), log(2.0 * M_PI)));
+        for (int p = 0; p < P; ++p) sh.inv_sigma[p] = __ddiv_rn(1.0, sh.net.sigma[p]);
     }
     if (tid < R) {
         const double rt = reaction_rate(sh.net, theta, tid);
@@ -739,7 +741,7 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
                     acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(dv, dv), v));
                     lv = __dadd_rn(lv, log(v));
                 } else {
-                    const double z = __ddiv_rn(__dsub_rn(yk[p], mu), sh.net.sigma[p]);
+                    const double z = div_by_recip(__dsub_rn(yk[p], mu), sh.net.sigma[p], sh.inv_sigma[p]);
                     acc = __dadd_rn(acc, __dmul_rn(z, z));
                 }
             }

@@ -166,9 +166,9 @@ extern "C" int pf_exp_variates(uint64_t seed, int64_t n, double *out) {
 }
 
 namespace {
-// Counts quotients where div_pos differs from the IEEE division, over n
-// pseudo-random pairs (numerators like Exp(1) variates, divisors spread over
-// 2^-60 .. 2^60).
+// Counts quotients where div_pos or div_by_recip differs from the IEEE
+// division, over n pseudo-random pairs (numerators like Exp(1) variates, with
+// a random sign for div_by_recip; divisors spread over 2^-60 .. 2^60).
 __global__ void div_check_kernel(uint64_t seed, int64_t n, unsigned long long *mismatch) {
     const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
     unsigned long long local = 0;
@@ -181,7 +181,13 @@ __global__ void div_check_kernel(uint64_t seed, int64_t n, unsigned long long *m
         const double num = 20.0 * pf::scaled_u53((a >> 11) + 1ull);
         const int e = static_cast<int>(b & 127u) - 60;
         const double den = ldexp(1.0 + pf::scaled_u53((b >> 11) + 1ull), e);
-        if (__double_as_longlong(pf::div_pos(num, den)) != __double_as_longlong(__ddiv_rn(num, den)))
+        const double ieee = __ddiv_rn(num, den);
+        if (__double_as_longlong(pf::div_pos(num, den)) != __double_as_longlong(ieee)) ++local;
+        // the weight's quotient by a fixed divisor with its rounded reciprocal
+        // (signed numerators)
+        const double sn = (b & 128u) ? -num : num;
+        if (__double_as_longlong(pf::div_by_recip(sn, den, __ddiv_rn(1.0, den))) !=
+            __double_as_longlong(__ddiv_rn(sn, den)))
             ++local;
     }
     if (local) atomicAdd(mismatch, local);

@@ -76,8 +76,9 @@ def test_exp_variates_match_oracle_bit_for_bit(pf):
 
 
 def test_waiting_time_division_matches_ieee(pf):
-    """The kernels divide E / a0 with a reciprocal seed, one Newton step and a
-    residual correction; over 10^8 pairs it must agree with the IEEE quotient
-    everywhere (a disagreement needs the exact quotient within ~2^-40 of a
-    rounding midpoint)."""
+    """The kernels' two divisions agree with the IEEE quotient on 10^8 pairs
+    each: the waiting time E / a0 (reciprocal seed, one Newton step, residual
+    correction: a disagreement needs the exact quotient within ~2^-50 ulp of a
+    rounding midpoint) and the Gaussian weight's (y - mu) / sigma from the
+    correctly rounded 1 / sigma (exact by Markstein's theorem)."""
     assert pf.pf_div_check(7, 100_000_000) == 0
