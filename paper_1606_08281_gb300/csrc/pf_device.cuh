@@ -60,8 +60,6 @@ struct SharedHead {
     int rem_j[2][kMaxRemnants];          // parked particle index
     uint32_t rem_draws[2][kMaxRemnants]; // its draw counter
     double rem_t[2][kMaxRemnants];       // its time
-    int bucket[16];
-    float rate_f[PF_MAX_REACTIONS];  // FP32 copy of rate[], for cost estimates only
     double inv_sigma[PF_MAX_OBS_DIM];  // 1 / sigma_p, correctly rounded
     ZigX zig;                 // ziggurat layer edges
     const ZigTab *zig_g;      // the full ziggurat table (global memory)
@@ -146,10 +144,10 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 
 // Simulate every particle of the filter from t_prev to t_end by Gillespie's
 // direct method (Supp. I, "Simulate X_t"; Sec. "The stochastic birth-death
-// Model": SSA).  Lanes take particles from a pool in the order `order`
-// (heaviest expected work first); each loop trip is one direct-method step of
-// every active lane.  Failure is reported through sh.status (PF_ST_BUDGET when
-// a particle needed more than `budget` draws); `fired` counts reactions.
+// Model": SSA).  Lanes take particles from a pool in the order `order`; each
+// loop trip is one direct-method step of every active lane.  Failure is
+// reported through sh.status (PF_ST_BUDGET when a particle needed more than
+// `budget` draws); `fired` counts reactions.
 template <int RM, int UM>
 __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, int N,
                              double t_prev, double t_end, uint32_t key0, uint32_t key1,
@@ -409,23 +407,6 @@ __device__ __forceinline__ double grid20(double e) {
     return __dmul_rn(rint(__dmul_rn(e, 1048576.0)), 1.0 / 1048576.0);
 }
 
-// Expected-work bucket of particle j for the interval (FP32, ordering only):
-// 15 - min(15, 1 + floor(log2(a0(x_j) * dt))), so heavy particles come first.
-__device__ __forceinline__ int cost_bucket(const SharedHead &sh, const int *xs, int Np, int j,
-                                           float dt) {
-    Lane<0> L;
-    L.xs = xs;
-    L.Np = Np;
-    L.j = j;
-    float a0 = 0.f;
-    for (int r = 0; r < sh.net.R; ++r)
-        a0 += sh.rate_f[r] * static_cast<float>(combos<0>(r, sh.net, L));
-    const float est = a0 * dt;
-    int b = 0;
-    if (est >= 1.f) b = min(15, ((__float_as_int(est) >> 23) & 0xFF) - 127 + 1);
-    return 15 - b;
-}
-
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     z ^= z >> 30;
     z *= 0xBF58476D1CE4E5B9ull;
@@ -575,7 +556,6 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
     if (tid < R) {
         const double rt = reaction_rate(sh.net, theta, tid);
         sh.rate[tid] = rt;
-        sh.rate_f[tid] = static_cast<float>(rt);
     }
     __syncthreads();
     if (!sh.valid) {
@@ -688,26 +668,15 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
 
         const double t_k = job.obs_times[k];
         if (t_k > t_prev) {
-            // pool order: counting sort of the particles by expected work, heaviest first
-            const float dt = static_cast<float>(t_k - t_prev);
-            if (tid < 16) sh.bucket[tid] = 0;
-            __syncthreads();
-            for (int j = tid; j < N; j += B) atomicAdd(&sh.bucket[cost_bucket(sh, xs, Np, j, dt)], 1);
-            __syncthreads();
+            // pool order: the particles in index order (the refill loop and the
+            // tail consolidation absorb their unequal costs; sorting them
+            // heaviest first no longer paid for its two passes)
             if (tid == 0) {
-                int run = 0;
-                for (int b = 0; b < 16; ++b) {
-                    const int c = sh.bucket[b];
-                    sh.bucket[b] = run;
-                    run += c;
-                }
                 sh.pool_next = 0;
                 sh.rem_n[0] = 0;
                 sh.rem_n[1] = 0;
             }
-            __syncthreads();
-            for (int j = tid; j < N; j += B)
-                order[atomicAdd(&sh.bucket[cost_bucket(sh, xs, Np, j, dt)], 1)] = j;
+            for (int j = tid; j < N; j += B) order[j] = j;
             __syncthreads();
             ssa_interval<RM, UM>(sh, xs, order, Np, N, t_prev, t_k, key0, key1, lane, m32,
                                  job.budget, fired);
