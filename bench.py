@@ -67,9 +67,9 @@ ZIG_FLOPS = 1.0 + P_WEDGE * (7.0 + P_WEDGE_OPEN * FP64_FLOPS_EXP + 0.5) + P_TAIL
 
 # DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on the 152-theta
-# case of the same kernel (458 752 + 0 bytes) scaled by the filters processed
+# case of the same kernel (531 968 + 0 bytes) scaled by the filters processed
 # (x 4096/152).
-FILTER_TRAFFIC_BYTES = 12.36e6
+FILTER_TRAFFIC_BYTES = 14.34e6
 
 
 def flops_per_event(R: int) -> float:
