@@ -117,6 +117,24 @@ def test_particle_filter_unbiased_for_fsp_likelihood():
     check_filter_unbiased(fsp)
 
 
+def test_gene_expression_filter_unbiased_against_fsp(S=300):
+    """The gene-expression filter (the bench's network) against its exact
+    likelihood: on the first 8 observation times the FSP box 0..16 x 0..250
+    holds all but ~1e-12 of the mass, and mean exp(ll_PF - L_FSP) = 1."""
+    w = W.gene_expression()
+    y = w.observations()[:1, :8]
+    times = w.obs_times[:8]
+    for th in [w.theta_star, np.array([0.2, 0.1, 1.5, 0.02])]:
+        L, leak = fsp.loglik(w.net, th, w.x0, [16, 250], times, y[0], w.C, w.sigma)
+        assert abs(leak) < 1e-10
+        lls = np.array([pf_oracle.pf_loglik(w.net, [th], w.x0, times, y, w.C, w.sigma, 200,
+                                            700 + s)["loglik"][0] for s in range(S)])
+        z = np.exp(lls - L)
+        se = z.std(ddof=1) / np.sqrt(S)
+        assert abs(z.mean() - 1.0) < 4 * se + 1e-3, (th, z.mean(), se)
+        assert lls.mean() <= L + 4 * lls.std(ddof=1) / np.sqrt(S)
+
+
 # ------------------------------------------------------------- mutants ----
 MUTANTS = {
     "propagate_transposed": ("splinalg.expm_multiply(Q.T.tocsc() * dt, alpha)",
