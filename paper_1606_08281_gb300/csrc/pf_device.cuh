@@ -402,6 +402,11 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
     }
 }
 
+// c != +-0, tested on its bits.
+__device__ __forceinline__ bool nonzero(double c) {
+    return (static_cast<unsigned long long>(__double_as_longlong(c)) << 1) != 0ull;
+}
+
 // e rounded to a multiple of 2^-20, ties to even (exact scalings by 2^20).
 __device__ __forceinline__ double grid20(double e) {
     return __dmul_rn(rint(__dmul_rn(e, 1048576.0)), 1.0 / 1048576.0);
@@ -698,14 +703,19 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
         for (int j = tid; j < N; j += B) {
             double acc = 0.0, lv = 0.0;
             for (int p = 0; p < P; ++p) {
+                // terms with a zero coefficient add +-0 exactly and are skipped
+                // (a warp-uniform test on the coefficient's bits); counts
+                // convert to double on the integer pipes
                 double mu = sh.net.obs_offset[p];
                 for (int u = 0; u < U; ++u)
-                    mu = __dadd_rn(mu, __dmul_rn(sh.net.C[p][u], static_cast<double>(xs[u * Np + j])));
+                    if (nonzero(sh.net.C[p][u]))
+                        mu = __dadd_rn(mu, __dmul_rn(sh.net.C[p][u], count_to_double(xs[u * Np + j])));
                 if (svar) {
                     double v = __dmul_rn(sh.net.sigma[p], sh.net.sigma[p]);
                     for (int u = 0; u < U; ++u)
-                        v = __dadd_rn(v, __dmul_rn(sh.net.obs_var[p][u],
-                                                   static_cast<double>(xs[u * Np + j])));
+                        if (nonzero(sh.net.obs_var[p][u]))
+                            v = __dadd_rn(v, __dmul_rn(sh.net.obs_var[p][u],
+                                                       count_to_double(xs[u * Np + j])));
                     const double dv = __dsub_rn(yk[p], mu);
                     acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(dv, dv), v));
                     lv = __dadd_rn(lv, log(v));

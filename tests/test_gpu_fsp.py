@@ -130,3 +130,16 @@ def test_gpu_filter_unbiased_for_gpu_fsp(pf):
     z = np.exp(r["loglik"] - L)
     se = z.std(ddof=1) / np.sqrt(len(z))
     assert abs(z.mean() - 1.0) < 4 * se + 1e-3, (z.mean(), se)
+
+
+def test_full_size_telegraph_sampled(pf):
+    """The bench's launch: all 4096 theta rows of the telegraph workload at
+    once; 16 sampled rows against the oracle."""
+    w = W.telegraph()
+    th = w.thetas()
+    g = pf.pf_fsp_loglik(w.net, th, w.x0, w.fsp_box, w.obs_times, w.observations(), w.C, w.sigma)
+    assert (g["status"] == 0).all()
+    pick = np.random.default_rng(5).choice(len(th), 16, replace=False)
+    tot, _, _ = fsp.loglik_batch(w.net, th[pick], w.x0, w.fsp_box, w.obs_times, w.observations(),
+                                 w.C, w.sigma)
+    np.testing.assert_allclose(g["loglik"][pick], tot, rtol=RTOL, atol=0)

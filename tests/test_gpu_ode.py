@@ -109,3 +109,18 @@ def test_prior_draws_finish(pf):
     g = pf.pf_erk_loglik(th, w.patterns, w.obs_times, w.observations(), max_steps=20000)
     assert set(np.unique(g["status"]).tolist()) <= {0, pf.PF_ST_BUDGET}
     assert np.isfinite(g["loglik"][g["status"] == 0]).all()
+
+
+def test_full_size_erk_sampled(pf):
+    """The bench's launch: all 4096 theta rows x 6 patterns at the default
+    tolerance; 6 sampled rows against the oracle within 100x the bound."""
+    w = W.erk()
+    th = w.thetas()
+    y = w.observations()
+    g = pf.pf_erk_loglik(th, w.patterns, w.obs_times, y)
+    assert (g["status"] == 0).all()
+    for m in np.random.default_rng(6).choice(len(th), 6, replace=False):
+        _, per = ode.loglik(th[m], w.patterns, w.obs_times, y)
+        Rm = ode.observe(th[m], w.patterns, w.obs_times)
+        tol = 100 * sum(tolerance(th[m], Rm[p], y[p]) for p in range(len(y))) + 1e-9 * abs(per.sum())
+        assert abs(g["loglik"][m] - per.sum()) <= tol, (m, g["loglik"][m], per.sum(), tol)
