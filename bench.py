@@ -67,9 +67,9 @@ ZIG_FLOPS = 1.0 + P_WEDGE * (7.0 + P_WEDGE_OPEN * FP64_FLOPS_EXP + 0.5) + P_TAIL
 
 # DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on the 152-theta
-# case of the same kernel (531 968 + 0 bytes) scaled by the filters processed
+# case of the same kernel (611 072 + 0 bytes) scaled by the filters processed
 # (x 4096/152).
-FILTER_TRAFFIC_BYTES = 14.34e6
+FILTER_TRAFFIC_BYTES = 16.47e6
 
 
 def flops_per_event(R: int) -> float:
@@ -265,6 +265,8 @@ def main() -> None:
                          "Poisson request stream, continuous batching vs a plain FIFO server; "
                          "fsp: the exact FSP likelihood of a workload with an FSP box "
                          "(telegraph, birth_death); ode: the deterministic Erk-model likelihood")
+    ap.add_argument("--ode-theta", type=int, default=4096,
+                    help="--mode ode: theta rows per launch (the Erk batch size)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--autotune", action="store_true",
@@ -544,6 +546,7 @@ def run_ode(a, pf) -> None:
     """The Erk-model likelihood of every theta row (one JSON line)."""
     import torch
     w = W.erk()
+    w.M = a.ode_theta
     dev = torch.device("cuda", torch.cuda.current_device())
     th = torch.from_numpy(w.thetas()).to(dev)
     yd = torch.from_numpy(w.observations()).to(dev)
