@@ -160,3 +160,26 @@ def test_batch_early_rejection_matches_plain(pf, ctx, problems):
     assert (reqs[0].status == ref["status"]).all()
     assert np.array_equal(reqs[0].loglik, ref["loglik"])
     assert (reqs[0].status == pf.PF_ST_REJECTED).sum() == (full["loglik"] < thr).sum()
+
+
+def test_batch_covers_every_tier(pf):
+    """Requests on networks of every kernel group (reaction tiers with state
+    in registers or in shared memory, and a global-slab population) in one
+    batch equal their plain calls bit for bit."""
+    from test_gpu_parity import tier_problem
+    c = pf.pf_ctx_create(mem_budget_bytes=0, n_slots=2, max_particles=8192)
+    try:
+        reqs = []
+        for i, (kind, N) in enumerate([("r4_u5", 128), ("r8_u4", 128), ("r8_u6", 256),
+                                       ("r15_u8", 128), ("r15_u8", 6000)]):
+            net, th, x0, times, y, C, sigma = tier_problem(kind)
+            pid = pf.pf_ctx_load_problem(c, net, th.shape[1], x0, times, y, C, sigma)
+            reqs.append((pf.Request(pid, th[:3], N, 50 + i), net, th[:3], x0, times, y, C, sigma, N,
+                         50 + i))
+        pf.pf_ctx_run_batch(c, [r[0] for r in reqs])
+        for r, net, th, x0, times, y, C, sigma, N, seed in reqs:
+            ref = pf.pf_loglik(net, th, x0, times, y, C, sigma, N, seed)
+            assert (r.status == ref["status"]).all()
+            assert np.array_equal(r.loglik, ref["loglik"]), (N, r.loglik, ref["loglik"])
+    finally:
+        pf.pf_ctx_destroy(c)

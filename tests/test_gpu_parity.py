@@ -258,3 +258,48 @@ def test_full_size_gene_expression_sampled(pf):
                             w.N, w.filter_seed, theta_ids=pick)
     sub = {k: g[k][pick] for k in ("loglik", "status", "ll_traj", "events", "digest")}
     assert_parity(sub, o)
+
+
+def tier_problem(kind: str):
+    """Seeded networks that land in each kernel tier: (reactions <= 4, more than
+    4 species), (5..8 reactions, <= 4 species: state in registers), (5..8
+    reactions, 6 species), (9..16 reactions, 8 species).  Observed species 0
+    and 1 from one oracle path at a prior draw, sigma = 2."""
+    if kind == "r4_u5":
+        reac = np.zeros((4, 5), np.int32)
+        prod = np.zeros((4, 5), np.int32)
+        prod[0, 0] = 1                                  # 0 -> S0
+        reac[1, 0], prod[1, 1], prod[1, 4] = 1, 1, 1    # S0 -> S1 + S4
+        reac[2, 1], prod[2, 2] = 1, 1                   # S1 -> S2
+        reac[3, 2], reac[3, 4], prod[3, 3] = 1, 1, 1    # S2 + S4 -> S3
+        net = {"reactants": reac, "products": prod, "rate_index": None}
+        lo, hi = np.array([5.0, 0.1, 0.1, 1e-3]), np.array([50.0, 1.0, 1.0, 1e-2])
+        U = 5
+    else:
+        U, n0, n2 = {"r8_u4": (4, 2, 2), "r8_u6": (6, 1, 1), "r15_u8": (8, 3, 4)}[kind]
+        for seed in range(4100, 4200):      # the first seed whose network meets the generator's rules
+            try:
+                net = W.cascade_network(seed=seed, U=U, n0=n0, n1=U, n2=n2)
+                break
+            except AssertionError:
+                continue
+        lo, hi = net["prior_lo"], net["prior_hi"]
+    rng = np.random.default_rng(41)
+    x0 = rng.integers(0, 30, size=U).astype(np.int32)
+    th = W.log_uniform(np.random.default_rng(42), lo, hi, 5)
+    times = np.arange(1, 6, dtype=np.float64)
+    C = np.zeros((2, U))
+    C[0, 0] = C[1, 1] = 1.0
+    s, _, _ = pf_oracle.ssa_paths(net, th[0], x0, times, 2, seed=43)
+    y = s[:, :, :2].astype(np.float64) + np.random.default_rng(44).normal(size=(2, 5, 2)) * 2.0
+    return net, th, x0, times, y, C, np.array([2.0, 2.0])
+
+
+@pytest.mark.parametrize("kind,N", [("r4_u5", 200), ("r8_u4", 200), ("r8_u6", 200),
+                                    ("r15_u8", 200), ("r15_u8", 6000)])
+def test_reaction_tiers(pf, kind, N):
+    """Every kernel tier (and a tier-16 population in the global slab)."""
+    net, th, x0, times, y, C, sigma = tier_problem(kind)
+    g, o = run_both(pf, net, th, x0, times, y, C, sigma, N, 45, final_states=True)
+    assert_parity(g, o, final_states=True)
+    assert int(g["events"].sum()) > 1000
