@@ -589,7 +589,7 @@ def run_ode(a, pf) -> None:
             "dp_steps_per_launch": steps, "clocks": clk,
             "roofline": {"bound": "alu", "achieved": ops_rate / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP64 ops/s", "frac": ops_rate / peak_ops, "traffic": None,
-                         "kernel": "erk_kernel (FP64 pipe; one thread per theta and pattern)",
+                         "kernel": "erk_kernel (FP64 pipe; a lane pair per theta and pattern)",
                          "fp64_ops_per_dp_step": ODE_OPS_PER_STEP}}
     print(json.dumps(line), flush=True)
 

@@ -4,13 +4,15 @@
 // particle filter: solve the ODE for theta and score the trajectory under the
 // observation model (Sec. "A realistic example").
 //
-// GB300 layout: one thread per (theta row, input pattern), many per SM; each
-// integrates the 14 concentrations with the explicit Dormand-Prince 5(4)
+// GB300 layout: a pair of lanes per (theta row, input pattern), many per SM;
+// each pair integrates the 14 concentrations (half of the right-hand side and
+// of the stage combinations on each lane, the halves exchanged by shuffles)
+// with the explicit Dormand-Prince 5(4)
 // pair (Dormand & Prince, J. Comput. Appl. Math. 6, 1980; FSAL, step control
 // as in Hairer, Norsett & Wanner, "Solving ODEs I", Sec. II.4), stepping
 // exactly onto every input switch time (the right-hand side jumps there) and
 // every observation time, where it adds log N(y; R(x), sigma^2) with the
-// FRET ratio R.  Stage vectors live in the thread's local memory (L1).  The
+// FRET ratio R.  Each lane keeps the stage vectors of its own components.  The
 // work is FP64 arithmetic: per step six right-hand-side evaluations (with
 // their Michaelis-Menten quotients) and the stage combinations.  A trajectory
 // that needs more than max_steps steps (a stiff or diverging theta for an
@@ -49,27 +51,75 @@ struct OdeArgs {
     uint32_t *steps_f;         // [M * NP] or null
 };
 
-// Right-hand side of the reaction equations; th = theta, u = egf input.
-__device__ __forceinline__ void erk_rhs(const double *x, const double *th, double u, double *dx) {
-    const double EGFR = x[0], EGFRa = x[1], Ras = x[2], Rasa = x[3], Raf = x[4], Rafa = x[5];
-    const double MEK = x[6], MEKa = x[7], ERK = x[8], ERKa = x[9], NFB = x[10], NFBa = x[11];
-    const double dusp = x[12], DUSP = x[13];
-    const double v1 = th[0] * u * EGFR - th[1] * EGFRa;
-    const double v2 = th[2] * EGFRa * Ras / (th[3] + Ras) - th[4] * Rasa / (th[5] + Rasa);
-    const double kn2 = th[8] * th[8];
-    const double v3 = th[6] * Rasa * Raf / (th[7] + Raf) * kn2 / (kn2 + NFBa * NFBa) -
-                      th[9] * Rafa / (th[10] + Rafa);
-    const double v4 = th[11] * Rafa * MEK / (th[12] + MEK) - th[13] * MEKa / (th[14] + MEKa);
-    const double v5 = th[15] * MEKa * ERK / (th[16] + ERK) - th[17] * DUSP * ERKa / (th[18] + ERKa);
-    const double e2 = EGFRa * EGFRa;
-    const double v6 = th[19] * ERKa * NFB / (th[20] + NFB) * e2 / (th[21] * th[21] + e2) -
-                      th[22] * NFBa / (th[23] + NFBa);
+// The reaction equations of the model (Supp. "Reaction Equations"): each pair
+// of an inactive and an active form changes by -v and +v, v a difference of
+// Michaelis-Menten terms (v3 and v6 with Hill-type feedback factors).
+//
+// Each problem (theta row, pattern) runs on a pair of adjacent lanes: half 0
+// owns the components 0..7 (EGFR .. MEK*, fluxes 1-4), half 1 the components
+// 8..13 (ERK .. DUSP, fluxes 5-6 and the dusp equations).  So that the two
+// lanes run the same instructions (they share a warp), each evaluates three
+// Michaelis-Menten slots of one common form
+//   F = kA xa xb (hc0 + hc1 z^2) / ((KA + xb)(hd + z^2)) - kB xc xd / (KB + xd)
+// whose constants and operands are chosen per half:
+//   half 0: v2, v3 (Raf inhibition by Erk*-dependent feedback, Hill z = x11),
+//           v4; plus v1 (linear);
+//   half 1: v5 (Erk dephosphorylation by DUSP: xc = x13), v6 (Hill z = x1),
+//           and the Erk*-induced dusp production (Hill z = x9, kB = 0).
+// Where a slot has no Hill factor, hc0 = hd = 1 and z = 0 make it exactly 1.
+constexpr int kOwn = 8;
+struct Slots {
+    double kA[3], KA[3], kB[3], KB[3];
+    double hc0[2], hc1[2], hd[2];    // slots 1 and 2
+    double c1, c2;                   // half 0: th0, th1 (v1); half 1: th24 a, a (dusp)
+};
+
+__device__ __forceinline__ void make_slots(int half, const double *th, Slots &s) {
     const double a = 0.30102999566398119521 / kThalf;      // log10(2) / T, as printed
-    const double ea2 = ERKa * ERKa;
-    dx[0] = -v1; dx[1] = v1; dx[2] = -v2; dx[3] = v2; dx[4] = -v3; dx[5] = v3;
-    dx[6] = -v4; dx[7] = v4; dx[8] = -v5; dx[9] = v5; dx[10] = -v6; dx[11] = v6;
-    dx[12] = th[24] * (1.0 + th[25] * ea2 / (th[26] + ea2)) * a - dusp * a;
-    dx[13] = dusp * a - DUSP * a;
+    const double kn2 = th[8] * th[8];
+    const bool h = half != 0;
+    s.kA[0] = h ? th[15] : th[2];  s.KA[0] = h ? th[16] : th[3];
+    s.kB[0] = h ? th[17] : th[4];  s.KB[0] = h ? th[18] : th[5];
+    s.kA[1] = h ? th[19] : th[6];  s.KA[1] = h ? th[20] : th[7];
+    s.kB[1] = h ? th[22] : th[9];  s.KB[1] = h ? th[23] : th[10];
+    s.hc0[0] = h ? 0.0 : kn2;      s.hc1[0] = h ? 1.0 : 0.0;   s.hd[0] = h ? th[21] * th[21] : kn2;
+    s.kA[2] = h ? th[24] * th[25] * a : th[11];  s.KA[2] = h ? 0.0 : th[12];
+    s.kB[2] = h ? 0.0 : th[13];    s.KB[2] = h ? 1.0 : th[14];
+    s.hc0[1] = h ? 0.0 : 1.0;      s.hc1[1] = h ? 1.0 : 0.0;   s.hd[1] = h ? th[26] : 1.0;
+    s.c1 = h ? th[24] * a : th[0]; s.c2 = h ? a : th[1];
+}
+
+// The owner's components of the right-hand side at the full state x.
+__device__ __forceinline__ void rhs_pair(bool h, const Slots &s, const double *x, double u, double *d) {
+    // slot 0: v2 | v5
+    const double a0 = h ? x[7] : x[1], b0 = h ? x[8] : x[2], c0 = h ? x[13] : 1.0, e0 = h ? x[9] : x[3];
+    const double F0 = s.kA[0] * a0 * b0 / (s.KA[0] + b0) - s.kB[0] * c0 * e0 / (s.KB[0] + e0);
+    // slot 1: v3 | v6
+    const double a1 = h ? x[9] : x[3], b1 = h ? x[10] : x[4], z1 = h ? x[1] : x[11], e1 = h ? x[11] : x[5];
+    const double q1 = z1 * z1;
+    const double F1 = s.kA[1] * a1 * b1 * fma(s.hc1[0], q1, s.hc0[0]) / ((s.KA[1] + b1) * (s.hd[0] + q1)) -
+                      s.kB[1] * e1 / (s.KB[1] + e1);
+    // slot 2: v4 | dusp production
+    const double a2 = h ? 1.0 : x[5], b2 = h ? 1.0 : x[6], z2 = h ? x[9] : 0.0, e2 = h ? 1.0 : x[7];
+    const double q2 = z2 * z2;
+    const double F2 = s.kA[2] * a2 * b2 * fma(s.hc1[1], q2, s.hc0[1]) / ((s.KA[2] + b2) * (s.hd[1] + q2)) -
+                      s.kB[2] * e2 / (s.KB[2] + e2);
+    const double v1 = s.c1 * u * x[0] - s.c2 * x[1];
+    const double d12 = s.c1 + F2 - s.c2 * x[12], d13 = s.c2 * x[12] - s.c2 * x[13];
+    const double P0 = h ? F0 : v1, P1 = h ? F1 : F0;
+    d[0] = -P0; d[1] = P0; d[2] = -P1; d[3] = P1;
+    d[4] = h ? d12 : -F1; d[5] = h ? d13 : F1;
+    d[6] = -F2; d[7] = F2;
+}
+
+// Assemble the full 14-vector from the two halves' owned components.
+__device__ __forceinline__ void exchange(unsigned pmask, bool h, const double *own, double *full) {
+#pragma unroll
+    for (int c = 0; c < kOwn; ++c) {
+        const double theirs = __shfl_xor_sync(pmask, own[c], 1);
+        full[c] = h ? theirs : own[c];
+        if (c < 6) full[8 + c] = h ? own[c] : theirs;
+    }
 }
 
 __device__ __forceinline__ double fret(const double *x, const double *th) {
@@ -90,14 +140,28 @@ constexpr double B1 = 35.0 / 384.0, B3 = 500.0 / 1113.0, B4 = 125.0 / 192.0,
 constexpr double E1 = 71.0 / 57600.0, E3 = -71.0 / 16695.0, E4 = 71.0 / 1920.0,
                  E5 = -17253.0 / 339200.0, E6 = 22.0 / 525.0, E7 = -1.0 / 40.0;
 
-__global__ void __launch_bounds__(kThreads) erk_kernel(const OdeArgs a) {
-    // threads run pattern-major (g = p * M + m): the lanes of a warp share an
-    // input pattern, so they stop at the same switch times and diverge less
-    const int64_t g = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (g >= a.M * a.NP) return;
+// Threads come in pairs (g = t >> 1), pattern-major (g = p * M + m) so that
+// the lanes of a warp share an input pattern.  Both lanes of a pair take the
+// same decisions (the error norm is summed over both halves in either order,
+// which is commutative), so they stay converged; a row's result depends on
+// its own inputs only.
+//
+// MinBlocks = 0 leaves the register count to the compiler (no spills, 4 blocks
+// per SM); MinBlocks = 6 caps it so that 6 blocks fit (a few spills to L1).
+// The host takes the capped instance only when the whole grid then fits in
+// one wave and otherwise would not: a grid of fewer problems than the GPU
+// holds gains more from having all of them resident than the spills cost.
+template <int MinBlocks>
+__global__ void __launch_bounds__(kThreads, MinBlocks) erk_kernel(const OdeArgs a) {
+    const int64_t tg = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const int64_t g = tg >> 1;
+    const int half = static_cast<int>(tg & 1);
+    if (g >= a.M * a.NP) return;                    // both lanes of the pair leave together
+    const unsigned pmask = 3u << (threadIdx.x & 30u);
     const int p = static_cast<int>(g / a.M);
     const int64_t m = g - static_cast<int64_t>(p) * a.M;
     const int64_t f = m * a.NP + p;                 // result slot [m][p]
+    const bool up = half != 0;                      // the upper half of the pair
     double th[36];
     bool ok = true;
     for (int i = 0; i < 36; ++i) {
@@ -106,13 +170,23 @@ __global__ void __launch_bounds__(kThreads) erk_kernel(const OdeArgs a) {
     }
     ok = ok && th[33] < 1.0;                         // FRET efficiency E in (0, 1)
     if (!ok) {
-        a.ll_f[f] = __longlong_as_double(0x7FF8000000000000ll);
-        a.st_f[f] = PF_ST_INVALID_THETA;
-        if (a.steps_f) a.steps_f[f] = 0;
+        if (half == 0) {
+            a.ll_f[f] = __longlong_as_double(0x7FF8000000000000ll);
+            a.st_f[f] = PF_ST_INVALID_THETA;
+            if (a.steps_f) a.steps_f[f] = 0;
+        }
         return;
     }
-    double x[kNs] = {th[27], 0.0, 0.1, 0.0, 0.7, 0.0, 0.68, 0.0, 0.26, 0.0, th[28], 0.0, th[29], th[29]};
-    double k1[kNs], k2[kNs], k3[kNs], k4[kNs], k5[kNs], k6[kNs], k7[kNs], yt[kNs];
+    // yt: the full state at the stage points; after an accepted step it is the
+    // new state x, and x is read (k1 after an input switch, R at an
+    // observation time) only then, so x needs no copy of its own.
+    double yt[kNs] = {th[27], 0.0, 0.1, 0.0, 0.7, 0.0, 0.68, 0.0, 0.26, 0.0, th[28], 0.0, th[29], th[29]};
+    double k1[kOwn], k2[kOwn], k3[kOwn], k4[kOwn], k5[kOwn], k6[kOwn], k7[kOwn], yo[kOwn];
+    double xo[kOwn];                              // the owner's components of x
+#pragma unroll
+    for (int c = 0; c < kOwn; ++c) xo[c] = up ? (c < 6 ? yt[8 + c] : 0.0) : yt[c];
+    Slots sl;
+    make_slots(half, th, sl);
     const double *st = a.sw_t + a.sw_off[p];
     const int ns = a.sw_off[p + 1] - a.sw_off[p];
     const double *sv = a.sw_v + a.sw_off[p];
@@ -132,39 +206,57 @@ __global__ void __launch_bounds__(kThreads) erk_kernel(const OdeArgs a) {
         while (t < tk && status == PF_ST_OK) {
             const double tstop = (si < ns && st[si] < tk) ? st[si] : tk;
             if (fresh) {
-                erk_rhs(x, th, u, k1);
+                rhs_pair(up, sl, yt, u, k1);
                 fresh = false;
             }
-            // one Dormand-Prince step, clipped to the stop
             bool last = false;
             double hh = h;
             if (t + hh >= tstop) {
                 hh = tstop - t;
                 last = true;
             }
-            for (int i = 0; i < kNs; ++i) yt[i] = x[i] + hh * (A21 * k1[i]);
-            erk_rhs(yt, th, u, k2);
-            for (int i = 0; i < kNs; ++i) yt[i] = x[i] + hh * (A31 * k1[i] + A32 * k2[i]);
-            erk_rhs(yt, th, u, k3);
-            for (int i = 0; i < kNs; ++i) yt[i] = x[i] + hh * (A41 * k1[i] + A42 * k2[i] + A43 * k3[i]);
-            erk_rhs(yt, th, u, k4);
-            for (int i = 0; i < kNs; ++i)
-                yt[i] = x[i] + hh * (A51 * k1[i] + A52 * k2[i] + A53 * k3[i] + A54 * k4[i]);
-            erk_rhs(yt, th, u, k5);
-            for (int i = 0; i < kNs; ++i)
-                yt[i] = x[i] + hh * (A61 * k1[i] + A62 * k2[i] + A63 * k3[i] + A64 * k4[i] + A65 * k5[i]);
-            erk_rhs(yt, th, u, k6);
-            for (int i = 0; i < kNs; ++i)
-                yt[i] = x[i] + hh * (B1 * k1[i] + B3 * k3[i] + B4 * k4[i] + B5 * k5[i] + B6 * k6[i]);
-            erk_rhs(yt, th, u, k7);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c) yo[c] = xo[c] + hh * (A21 * k1[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k2);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] + hh * (A31 * k1[c] + A32 * k2[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k3);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] + hh * (A41 * k1[c] + A42 * k2[c] + A43 * k3[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k4);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] +
+                        hh * (A51 * k1[c] + A52 * k2[c] + A53 * k3[c] + A54 * k4[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k5);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] +
+                        hh * (A61 * k1[c] + A62 * k2[c] + A63 * k3[c] + A64 * k4[c] + A65 * k5[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k6);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] +
+                        hh * (B1 * k1[c] + B3 * k3[c] + B4 * k4[c] + B5 * k5[c] + B6 * k6[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k7);
             double err = 0.0;
-            for (int i = 0; i < kNs; ++i) {
-                const double ei = hh * (E1 * k1[i] + E3 * k3[i] + E4 * k4[i] + E5 * k5[i] + E6 * k6[i] +
-                                        E7 * k7[i]);
-                const double sc = a.atol + a.rtol * fmax(fabs(x[i]), fabs(yt[i]));
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c) {
+                const double ei = hh * (E1 * k1[c] + E3 * k3[c] + E4 * k4[c] + E5 * k5[c] + E6 * k6[c] +
+                                        E7 * k7[c]);
+                const double sc = a.atol + a.rtol * fmax(fabs(xo[c]), fabs(yo[c]));
                 const double r = ei / sc;
-                err += r * r;
+                if (!up || c < 6) err += r * r;
             }
+            err += __shfl_xor_sync(pmask, err, 1);   // both halves, commutative: identical sums
             err = sqrt(err / kNs);
             if (!isfinite(err)) {
                 status = PF_ST_NONFINITE;
@@ -176,10 +268,10 @@ __global__ void __launch_bounds__(kThreads) erk_kernel(const OdeArgs a) {
             }
             if (err <= 1.0) {                         // accept
                 t = last ? tstop : t + hh;
-                for (int i = 0; i < kNs; ++i) {
-                    x[i] = yt[i];
-                    k1[i] = k7[i];                    // first same as last
-                }
+#pragma unroll
+                for (int c = 0; c < kOwn; ++c) xo[c] = yo[c];
+#pragma unroll
+                for (int c = 0; c < kOwn; ++c) k1[c] = k7[c];   // first same as last
                 const double fac = err > 0.0 ? fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2))) : 5.0;
                 if (!last || hh * fac < h) h = hh * fac;
                 if (last && si < ns && st[si] == tstop) {   // the input switches here
@@ -191,13 +283,15 @@ __global__ void __launch_bounds__(kThreads) erk_kernel(const OdeArgs a) {
             }
         }
         if (status != PF_ST_OK) break;
-        const double R = fret(x, th);
+        const double R = fret(yt, th);          // yt = x after the last accepted step
         const double z = (yp[k] - R) / sigma;
         ll += lnorm - 0.5 * z * z;
     }
-    a.ll_f[f] = status == PF_ST_OK ? ll : -INFINITY;
-    a.st_f[f] = static_cast<uint8_t>(status);
-    if (a.steps_f) a.steps_f[f] = steps;
+    if (half == 0) {
+        a.ll_f[f] = status == PF_ST_OK ? ll : -INFINITY;
+        a.st_f[f] = static_cast<uint8_t>(status);
+        if (a.steps_f) a.steps_f[f] = steps;
+    }
 }
 
 __global__ void erk_reduce_kernel(const double *ll_f, const uint8_t *st_f, int64_t M, int NP,
@@ -323,7 +417,18 @@ extern "C" int pf_erk_loglik(const double *thetas, int64_t M, const double *swit
         ODE_CUDA(b_steps.alloc(sizeof(uint32_t) * F, s), "alloc steps");
         a.steps_f = static_cast<uint32_t *>(b_steps.p);
     }
-    pf::erk_kernel<<<(unsigned)((F + pf::kThreads - 1) / pf::kThreads), pf::kThreads, 0, s>>>(a);
+    const int64_t nblk = (2 * F + pf::kThreads - 1) / pf::kThreads;
+    int dev = 0, sms = 0, occ_plain = 0, occ_capped = 0;
+    ODE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    ODE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_plain, pf::erk_kernel<0>, pf::kThreads, 0),
+             "occupancy");
+    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_capped, pf::erk_kernel<6>, pf::kThreads, 0),
+             "occupancy");
+    if (nblk > (int64_t)occ_plain * sms && nblk <= (int64_t)occ_capped * sms)
+        pf::erk_kernel<6><<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
+    else
+        pf::erk_kernel<0><<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
     ODE_CUDA(cudaGetLastError(), "ode launch");
     pf::erk_reduce_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(a.ll_f, a.st_f, M, NP, d_ll, d_st);
     ODE_CUDA(cudaGetLastError(), "ode reduce launch");

@@ -124,3 +124,7 @@ def test_full_size_erk_sampled(pf):
         Rm = ode.observe(th[m], w.patterns, w.obs_times)
         tol = 100 * sum(tolerance(th[m], Rm[p], y[p]) for p in range(len(y))) + 1e-9 * abs(per.sum())
         assert abs(g["loglik"][m] - per.sum()) <= tol, (m, g["loglik"][m], per.sum(), tol)
+    # 4096 rows fit in one wave only with the register-capped kernel instance,
+    # 64 rows run on the uncapped one: the same rows give the same bits
+    sub = pf.pf_erk_loglik(th[:64], w.patterns, w.obs_times, y)
+    assert np.array_equal(sub["loglik"], g["loglik"][:64])
