@@ -269,6 +269,9 @@ def main() -> None:
                     help="--mode ode: theta rows per launch (the Erk batch size)")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--cluster", type=int, default=0,
+                    help="split each filter over a thread-block cluster of this many blocks "
+                         "(pf_options.cluster_blocks; 0 = one block per filter)")
     ap.add_argument("--autotune", action="store_true",
                     help="tune block size and launch order on a theta sample before timing")
     a = ap.parse_args()
@@ -319,12 +322,13 @@ def main() -> None:
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
-    launch = {"block_threads": 0, "schedule": pf.PF_SCHED_AUTO}
+    launch = {"block_threads": 0, "schedule": pf.PF_SCHED_AUTO, "cluster_blocks": a.cluster}
     if a.autotune:
         from paper_1606_08281_gb300 import autotune
         tuned = autotune.tune(w.net, th_np, w.x0, w.obs_times, y_np, w.C, w.sigma, w.N,
                               sample_filters=20 * 608, cache=None)
-        launch = {"block_threads": tuned["block_threads"], "schedule": tuned["schedule"]}
+        launch = {"block_threads": tuned["block_threads"], "schedule": tuned["schedule"],
+                  "cluster_blocks": a.cluster}
 
     def step():
         pf.pf_loglik(w.net, th, w.x0, w.obs_times, yd, w.C, w.sigma, w.N, w.filter_seed,
@@ -376,7 +380,7 @@ def main() -> None:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         pf.pf_loglik(w.net, th_pin.numpy(), w.x0, w.obs_times, y_pin.numpy(), w.C, w.sigma, w.N,
-                     w.filter_seed, out=host_out, model=w.model)
+                     w.filter_seed, out=host_out, model=w.model, cluster_blocks=a.cluster)
         e2e_times.append(time.perf_counter() - t0)
     if e2e_times:
         assert np.array_equal(host_out["loglik"], out["loglik"].cpu().numpy())

@@ -131,6 +131,20 @@ typedef struct {
  *   model         optional model extensions (pf_model; NULL = the basic
  *                 model: point-mass x0, rates theta[rate_index[r]], constant
  *                 observation variance).
+ *   cluster_blocks 0 or 1: one thread block per filter.  2..8
+ *                 (PF_MAX_CLUSTER_BLOCKS): each filter is split over a
+ *                 thread-block cluster of that many blocks, on as many SMs;
+ *                 block b simulates particles b*ceil(N/C) .. and the blocks
+ *                 exchange weight maxima, sums and integer-weight totals
+ *                 through distributed shared memory for the weights and the
+ *                 resampling.  States, ancestors, events and digests are those
+ *                 of the one-block filter bit for bit; the log-likelihood
+ *                 differs only in the summation order of the weights (last
+ *                 places).  For launches whose time is set by a few filters
+ *                 with many events (one block would leave the other SMs
+ *                 idle).  Every block must hold at least one particle
+ *                 (N > (C - 1) ceil(N / C)) and its share must fit in shared
+ *                 memory; otherwise PF_EINVAL.
  *   Diagnostics are defined only for filters whose status is PF_ST_OK.
  */
 /*
@@ -170,6 +184,7 @@ typedef struct {
     const double *obs_var;
 } pf_model;
 
+#define PF_MAX_CLUSTER_BLOCKS 8
 #define PF_SCHED_AUTO 0
 #define PF_SCHED_NATURAL 1
 #define PF_SCHED_HEAVY_FIRST 2
@@ -187,6 +202,7 @@ typedef struct {
     const uint32_t *row_order;
     double reject_below;
     const pf_model *model;
+    int32_t cluster_blocks;
 } pf_options;
 
 /*

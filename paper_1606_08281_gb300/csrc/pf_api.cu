@@ -248,8 +248,14 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
         a.zig = pf::zig_table_device(&ze);
         if (!a.zig) return cuda_fail(ze, "ziggurat table");
     }
+    const int CB = o.cluster_blocks;
+    if (CB < 0 || CB > PF_MAX_CLUSTER_BLOCKS)
+        return fail(PF_EINVAL, "cluster_blocks %d outside 0..%d", CB, PF_MAX_CLUSTER_BLOCKS);
+    const int Nb = CB > 1 ? (N + CB - 1) / CB : N;   // particles per block
+    if (CB > 1 && N - (CB - 1) * Nb < 1)
+        return fail(PF_EINVAL, "n_particles %d leaves a block of the %d-block cluster empty", N, CB);
     int B = o.block_threads;
-    if (B == 0) B = std::min(128, ((N + 31) / 32) * 32);
+    if (B == 0) B = std::min(128, ((Nb + 31) / 32) * 32);
     if (B < 32 || B > 128 || (B % 32)) return fail(PF_EINVAL, "block_threads %d must be a multiple of 32 in 32..128", B);
     const size_t smem = pf::filter_smem_bytes(N, a.net.U, o.digest != nullptr);
     int dev = 0, smem_max = 0, sms = 0;
@@ -258,6 +264,13 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     PF_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     // populations that do not fit on chip (with the block's static tables) go to global memory
     const bool on_chip = smem + pf::filter_static_smem() <= (size_t)smem_max;
+    if (CB > 1) {
+        const size_t cs = pf::cluster_smem_bytes(N, CB, a.net.U, o.digest != nullptr);
+        if (cs + pf::filter_static_smem() > (size_t)smem_max)
+            return fail(PF_EINVAL, "a %d-block cluster's share of %d particles does not fit in shared memory", CB, N);
+        if (M * (int64_t)T * CB > 0x7FFFFFFFll) return fail(PF_EINVAL, "M * T * cluster_blocks must be < 2^31");
+        a.cluster = CB;
+    }
 
     cudaStream_t s = static_cast<cudaStream_t>(o.stream);
     // observation times (always a host array): strictly increasing, >= 0, finite
@@ -330,7 +343,7 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     }
     DevBuf b_slab;
     int grid = 0;
-    if (!on_chip) {
+    if (!on_chip && CB <= 1) {
         grid = (int)std::min<int64_t>(F, pf::global_grid(sms));
         PF_CUDA(b_slab.alloc(smem * (size_t)grid, s), "alloc global populations");
     }

@@ -23,6 +23,7 @@
 // results then match a plain sequential FP64 restatement bit for bit, except
 // where CUDA's log/exp differ from another libm in the last place.
 #pragma once
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -43,6 +44,7 @@ constexpr int kParkLanes = 16;      // a warp below this many busy lanes parks i
 constexpr unsigned kFull = 0xFFFFFFFFu;
 constexpr uint32_t kResampleLane = 0xFFFFFFFFu;
 constexpr uint32_t kInitLane = 0xFFFFFFFEu;      // particle slot of the initial-state draws
+constexpr int kMaxCluster = 8;     // blocks of a cluster that share one filter
 
 struct SharedHead {
     NetTables net;
@@ -63,6 +65,12 @@ struct SharedHead {
     double inv_sigma[PF_MAX_OBS_DIM];  // 1 / sigma_p, correctly rounded
     ZigX zig;                 // ziggurat layer edges
     const ZigTab *zig_g;      // the full ziggurat table (global memory)
+    // exchange slot of a filter split over a thread-block cluster: each
+    // block's share, read by the others through distributed shared memory
+    double cx_lmax, cx_lsum;
+    unsigned long long cx_qtot, cx_fired, cx_dig;
+    int cx_status, cx_reject;
+    unsigned long long cx_cum[kMaxCluster];  // cumulative integer-weight totals per block
 };
 
 // ------------------------------------------------------------------ helpers
@@ -147,12 +155,14 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 // Model": SSA).  Lanes take particles from a pool in the order `order`; each
 // loop trip is one direct-method step of every active lane.  Failure is
 // reported through sh.status (PF_ST_BUDGET when a particle needed more than
-// `budget` draws); `fired` counts reactions.
+// `budget` draws); `fired` counts reactions.  Particle slot j of `xs` is
+// particle j0 + j of the filter (j0 > 0 when the filter is split over the
+// blocks of a cluster); the random stream is keyed by the latter.
 template <int RM, int UM>
 __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, int N,
                              double t_prev, double t_end, uint32_t key0, uint32_t key1,
                              uint32_t lane, uint32_t mrow, uint64_t budget,
-                             unsigned long long &fired) {
+                             unsigned long long &fired, uint32_t j0 = 0) {
     const int R = sh.net.R, U = sh.net.U;
     const uint32_t all = (R >= 32) ? 0xFFFFFFFFu : ((1u << R) - 1u);
     const long long t_end_bits = dbits(t_end);
@@ -244,7 +254,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
             // This draw's random words and the ziggurat's first attempt depend
             // on the draw counter alone: computed first, they overlap with the
             // propensities (used only if the step draws at all).
-            const Philox4 w = philox4x32_10(draws, static_cast<uint32_t>(L.j), lane, mrow,
+            const Philox4 w = philox4x32_10(draws, j0 + static_cast<uint32_t>(L.j), lane, mrow,
                                             key0, key1);
             const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
             const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
@@ -330,7 +340,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                 // tau = E / a0 with E ~ Exp(1) from the ziggurat (rare slow
                 // path: the whole algorithm again from the first word)
                 if (!fast)
-                    E = zig_exp(r0, draws, static_cast<uint32_t>(L.j), lane, mrow, key0, key1,
+                    E = zig_exp(r0, draws, j0 + static_cast<uint32_t>(L.j), lane, mrow, key0, key1,
                                 sh.zig.x, sh.zig_g);
                 ++draws;
                 const double tau = div_pos(E, a0);
@@ -421,13 +431,19 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z;
 }
 
-// Fingerprint of slot j after the simulation step of interval k.
-__device__ __forceinline__ uint64_t slot_digest(uint32_t k, uint32_t j, uint32_t anc,
-                                                const int *xs, int Np, int U) {
+// Fingerprint of particle slot j after the simulation step of interval k;
+// its state is column jl of xs (jl = j unless the filter is split over a
+// cluster).
+__device__ __forceinline__ uint64_t slot_digest_at(uint32_t k, uint32_t j, uint32_t anc,
+                                                   const int *xs, int Np, int U, int jl) {
     uint64_t h = mix64((static_cast<uint64_t>(k) << 32) | j);
     h = mix64(h ^ static_cast<uint64_t>(anc));
-    for (int u = 0; u < U; ++u) h = mix64(h ^ static_cast<uint64_t>(static_cast<uint32_t>(xs[u * Np + j])));
+    for (int u = 0; u < U; ++u) h = mix64(h ^ static_cast<uint64_t>(static_cast<uint32_t>(xs[u * Np + jl])));
     return h;
+}
+__device__ __forceinline__ uint64_t slot_digest(uint32_t k, uint32_t j, uint32_t anc,
+                                                const int *xs, int Np, int U) {
+    return slot_digest_at(k, j, anc, xs, Np, U, static_cast<int>(j));
 }
 
 // Block-wide reductions (every thread receives the result).
@@ -506,6 +522,92 @@ __device__ inline void block_scan_u64(unsigned long long *q, int N, SharedHead &
 }
 
 
+// Per-filter set-up by the whole block: the theta row's validity (sh.valid),
+// the Gaussian normaliser, 1 / sigma_p and the reaction rates; ends with a
+// __syncthreads().
+__device__ __forceinline__ void filter_setup(const double *theta, SharedHead &sh) {
+    const int tid = threadIdx.x;
+    const int d = sh.net.d, R = sh.net.R, P = sh.net.P;
+    if (tid == 0) {
+        int ok = 1;
+        for (int c = 0; c < d; ++c) {
+            const double v = theta[c];
+            if (!(isfinite(v) && v >= 0.0)) ok = 0;
+        }
+        sh.valid = ok;
+        sh.status = PF_ST_OK;
+        sh.ll = 0.0;
+        // log of the Gaussian normalising constant; with a state-dependent
+        // variance the log v_p terms sit in each particle's log-weight instead
+        double ln = 0.0;
+        if (!sh.net.obs_state_var)
+            for (int p = 0; p < P; ++p) ln = __dadd_rn(ln, log(sh.net.sigma[p]));
+        sh.lognorm = __dadd_rn(ln, __dmul_rn(0.5 * static_cast<double>(P), log(2.0 * M_PI)));
+        for (int p = 0; p < P; ++p) sh.inv_sigma[p] = __ddiv_rn(1.0, sh.net.sigma[p]);
+    }
+    if (tid < R) sh.rate[tid] = reaction_rate(sh.net, theta, tid);
+    __syncthreads();
+}
+
+// Initial state of particle j (column jl of xs): x0, or each count uniform on
+// x0..x0_hi (species group g = u >> 2 shares one Philox block; word u & 3).
+__device__ __forceinline__ void init_particle(const SharedHead &sh, int *xs, int Np, int jl,
+                                              uint32_t j, int traj, uint32_t m32, uint32_t key0,
+                                              uint32_t key1) {
+    const int U = sh.net.U;
+    if (sh.net.x0_random) {
+        for (int g = 0; g * 4 < U; ++g) {
+            const Philox4 w = philox4x32_10(j, kInitLane,
+                                            (static_cast<uint32_t>(traj) << 20) | static_cast<uint32_t>(g),
+                                            m32, key0, key1);
+            const uint32_t word[4] = {w.w0, w.w1, w.w2, w.w3};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int u = 4 * g + q;
+                if (u < U) {
+                    const uint64_t span = static_cast<uint64_t>(
+                        static_cast<int64_t>(sh.net.x0_hi[u]) - sh.net.x0[u] + 1);
+                    xs[u * Np + jl] = sh.net.x0[u] +
+                                      static_cast<int>((static_cast<uint64_t>(word[q]) * span) >> 32);
+                }
+            }
+        }
+    } else {
+        for (int u = 0; u < U; ++u) xs[u * Np + jl] = sh.net.x0[u];
+    }
+}
+
+// Gaussian log-weight exponent of the particle in column j of xs:
+// e_j = -1/2 sum_p ((y_p - mu_p) / sigma_p)^2 with mu_p = offset_p + (C x_j)_p;
+// with a state-dependent variance v_p = sigma_p^2 + sum_u V_pu x_u,
+// e_j = -1/2 sum_p ((y_p - mu_p)^2 / v_p + log v_p).  Terms with a zero
+// coefficient add +-0 exactly and are skipped (a warp-uniform test on the
+// coefficient's bits); counts convert to double on the integer pipes.
+__device__ __forceinline__ double log_weight(const SharedHead &sh, const int *xs, int Np, int j,
+                                             const double *yk, bool svar) {
+    const int P = sh.net.P, U = sh.net.U;
+    double acc = 0.0, lv = 0.0;
+    for (int p = 0; p < P; ++p) {
+        double mu = sh.net.obs_offset[p];
+        for (int u = 0; u < U; ++u)
+            if (nonzero(sh.net.C[p][u]))
+                mu = __dadd_rn(mu, __dmul_rn(sh.net.C[p][u], count_to_double(xs[u * Np + j])));
+        if (svar) {
+            double v = __dmul_rn(sh.net.sigma[p], sh.net.sigma[p]);
+            for (int u = 0; u < U; ++u)
+                if (nonzero(sh.net.obs_var[p][u]))
+                    v = __dadd_rn(v, __dmul_rn(sh.net.obs_var[p][u], count_to_double(xs[u * Np + j])));
+            const double dv = __dsub_rn(yk[p], mu);
+            acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(dv, dv), v));
+            lv = __dadd_rn(lv, log(v));
+        } else {
+            const double z = div_by_recip(__dsub_rn(yk[p], mu), sh.net.sigma[p], sh.inv_sigma[p]);
+            acc = __dadd_rn(acc, __dmul_rn(z, z));
+        }
+    }
+    return svar ? __dmul_rn(-0.5, __dadd_rn(acc, lv)) : __dmul_rn(-0.5, acc);
+}
+
 // One filter -- one (theta row, observed trajectory) pair -- through all K
 // observation times (Supp. I, algorithm "Likelihood Approximation using particle
 // filter").  Called by every thread of the block.  Preconditions: sh.net and
@@ -538,31 +640,9 @@ struct FilterJob {
 template <int RM, int UM>
 __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *arrays) {
     const int tid = threadIdx.x, B = blockDim.x;
-    const int d = sh.net.d, R = sh.net.R, U = sh.net.U, P = sh.net.P;
+    const int U = sh.net.U, P = sh.net.P;
     const int N = job.N, K = job.K;
-    const double *theta = job.theta;
-    if (tid == 0) {
-        int ok = 1;
-        for (int c = 0; c < d; ++c) {
-            const double v = theta[c];
-            if (!(isfinite(v) && v >= 0.0)) ok = 0;
-        }
-        sh.valid = ok;
-        sh.status = PF_ST_OK;
-        sh.ll = 0.0;
-        // log of the Gaussian normalising constant; with a state-dependent
-        // variance the log v_p terms sit in each particle's log-weight instead
-        double ln = 0.0;
-        if (!sh.net.obs_state_var)
-            for (int p = 0; p < P; ++p) ln = __dadd_rn(ln, log(sh.net.sigma[p]));
-        sh.lognorm = __dadd_rn(ln, __dmul_rn(0.5 * static_cast<double>(P), log(2.0 * M_PI)));
-        for (int p = 0; p < P; ++p) sh.inv_sigma[p] = __ddiv_rn(1.0, sh.net.sigma[p]);
-    }
-    if (tid < R) {
-        const double rt = reaction_rate(sh.net, theta, tid);
-        sh.rate[tid] = rt;
-    }
-    __syncthreads();
+    filter_setup(job.theta, sh);
     if (!sh.valid) {
         if (tid == 0) {
             *job.ll_out = __longlong_as_double(0x7FF8000000000000ll);
@@ -592,31 +672,8 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
     const uint32_t m32 = job.mrow;
     const int traj = job.traj;
 
-    // initial particles: x0, or each count uniform on x0..x0_hi (species
-    // group g = u >> 2 shares one Philox block; word u & 3)
-    for (int j = tid; j < N; j += B) {
-        if (sh.net.x0_random) {
-            for (int g = 0; g * 4 < U; ++g) {
-                const Philox4 w = philox4x32_10(static_cast<uint32_t>(j), kInitLane,
-                                                (static_cast<uint32_t>(traj) << 20) |
-                                                    static_cast<uint32_t>(g),
-                                                m32, key0, key1);
-                const uint32_t word[4] = {w.w0, w.w1, w.w2, w.w3};
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int u = 4 * g + q;
-                    if (u < U) {
-                        const uint64_t span = static_cast<uint64_t>(
-                            static_cast<int64_t>(sh.net.x0_hi[u]) - sh.net.x0[u] + 1);
-                        xs[u * Np + j] = sh.net.x0[u] +
-                                         static_cast<int>((static_cast<uint64_t>(word[q]) * span) >> 32);
-                    }
-                }
-            }
-        } else {
-            for (int u = 0; u < U; ++u) xs[u * Np + j] = sh.net.x0[u];
-        }
-    }
+    // initial particles: x0, or each count uniform on x0..x0_hi
+    for (int j = tid; j < N; j += B) init_particle(sh, xs, Np, j, j, traj, m32, key0, key1);
     __syncthreads();
     unsigned long long fired = 0, dig = 0;
     double t_prev = 0.0;
@@ -694,37 +751,12 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
                 dig += slot_digest(static_cast<uint32_t>(k), static_cast<uint32_t>(j),
                                    static_cast<uint32_t>(anc[j]), xs, Np, U);
 
-        // Gaussian log-weight exponent e_j = -1/2 sum_p ((y_p - mu_p) / sigma_p)^2,
-        // mu_p = offset_p + (C x_j)_p; with a state-dependent variance
-        // v_p = sigma_p^2 + sum_u V_pu x_u, e_j = -1/2 sum_p ((y_p - mu_p)^2 / v_p + log v_p)
+        // Gaussian log-weight exponents (Supp. I, "Compute weights")
         const double *yk = job.y + static_cast<int64_t>(k) * P;
         const bool svar = sh.net.obs_state_var != 0;
         double lmax = -INFINITY;
         for (int j = tid; j < N; j += B) {
-            double acc = 0.0, lv = 0.0;
-            for (int p = 0; p < P; ++p) {
-                // terms with a zero coefficient add +-0 exactly and are skipped
-                // (a warp-uniform test on the coefficient's bits); counts
-                // convert to double on the integer pipes
-                double mu = sh.net.obs_offset[p];
-                for (int u = 0; u < U; ++u)
-                    if (nonzero(sh.net.C[p][u]))
-                        mu = __dadd_rn(mu, __dmul_rn(sh.net.C[p][u], count_to_double(xs[u * Np + j])));
-                if (svar) {
-                    double v = __dmul_rn(sh.net.sigma[p], sh.net.sigma[p]);
-                    for (int u = 0; u < U; ++u)
-                        if (nonzero(sh.net.obs_var[p][u]))
-                            v = __dadd_rn(v, __dmul_rn(sh.net.obs_var[p][u],
-                                                       count_to_double(xs[u * Np + j])));
-                    const double dv = __dsub_rn(yk[p], mu);
-                    acc = __dadd_rn(acc, __ddiv_rn(__dmul_rn(dv, dv), v));
-                    lv = __dadd_rn(lv, log(v));
-                } else {
-                    const double z = div_by_recip(__dsub_rn(yk[p], mu), sh.net.sigma[p], sh.inv_sigma[p]);
-                    acc = __dadd_rn(acc, __dmul_rn(z, z));
-                }
-            }
-            const double e = svar ? __dmul_rn(-0.5, __dadd_rn(acc, lv)) : __dmul_rn(-0.5, acc);
+            const double e = log_weight(sh, xs, Np, j, yk, svar);
             wbuf[j] = e;
             lmax = fmax(lmax, e);
         }
@@ -776,6 +808,241 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
             for (int u = 0; u < U; ++u) job.fs_out[static_cast<int64_t>(j) * U + u] = xs[u * Np + j];
     }
     __syncthreads();
+}
+
+
+// Bytes of one block's share of a filter split over C blocks of a cluster:
+// Np = ceil(N / C) particle columns of weights / prefix sums (8 B), states
+// [U] and staged states [U] (4 B each), pool order / ancestors (4 B), and the
+// ancestors kept for the digest (4 B).
+__host__ __device__ __forceinline__ size_t cluster_share_bytes(int N, int C, int U, bool digest) {
+    const size_t Np = static_cast<size_t>((N + C - 1) / C);
+    return Np * (8 + 8 * static_cast<size_t>(U) + 4 + (digest ? 4 : 0)) + 16;
+}
+
+// One filter split over the C blocks of a thread-block cluster (GB300: the C
+// blocks run on C SMs at once and read each other's shared memory).  Block
+// `rank` owns the particles j0 .. j0 + n - 1, j0 = rank Np, Np = ceil(N / C),
+// and simulates them exactly as run_filter would (the random stream is keyed
+// by the particle's index in the filter).  The steps that need the whole
+// population exchange one slot per block through distributed shared memory:
+//   A: the blocks' maxima of the log-weights and their statuses;
+//   B: their sums of exp(e - max) and their integer-weight totals, from
+//      which every block forms the cumulative totals and shifts its local
+//      prefix sums to the global ones;
+//   C: the global prefix sums are in place (and block 0's early-rejection
+//      decision is published);
+//   D (next interval): every block has found its particles' ancestors by a
+//      search of the owning block's prefix sums and copied their states.
+// The integer weights, their prefix sums, the ancestors and so the states and
+// the digest are those of the one-block filter bit for bit; the likelihood
+// differs only in the order of the sum of exp(e - max) (block sums added in
+// rank order).  Every decision to leave the loop is taken from exchanged
+// values after a cluster barrier, so all blocks pass the same barriers.
+// Requires n >= 1 in every block (N > (C - 1) ceil(N / C)); checked by the host.
+template <int RM, int UM>
+__device__ void run_filter_cluster(const FilterJob &job, SharedHead &sh, unsigned char *arrays) {
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = static_cast<int>(cl.num_blocks());
+    const int rank = static_cast<int>(cl.block_rank());
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int U = sh.net.U, P = sh.net.P;
+    const int N = job.N, K = job.K;
+    const int Np = (N + C - 1) / C;
+    const int j0 = rank * Np;
+    const int n = min(Np, N - j0);
+    filter_setup(job.theta, sh);
+    if (!sh.valid) {           // the same row in every block: all leave here
+        if (tid == 0 && rank == 0) {
+            *job.ll_out = __longlong_as_double(0x7FF8000000000000ll);
+            *job.st_out = PF_ST_INVALID_THETA;
+            *job.ev_out = 0;
+            if (job.dg_out) *job.dg_out = 0;
+        }
+        __syncthreads();
+        return;
+    }
+    const bool want_digest = job.dg_out != nullptr;
+    double *wbuf = reinterpret_cast<double *>(arrays);
+    unsigned long long *qbuf = reinterpret_cast<unsigned long long *>(arrays);
+    int *xs = reinterpret_cast<int *>(wbuf + Np);
+    int *order = xs + U * Np;
+    int *stage = order + Np;
+    int *anc = stage + U * Np;
+
+    const uint32_t key0 = static_cast<uint32_t>(job.seed);
+    const uint32_t key1 = static_cast<uint32_t>(job.seed >> 32);
+    const uint32_t m32 = job.mrow;
+    const int traj = job.traj;
+    for (int jl = tid; jl < n; jl += B)
+        init_particle(sh, xs, Np, jl, static_cast<uint32_t>(j0 + jl), traj, m32, key0, key1);
+    __syncthreads();
+
+    unsigned long long fired = 0, dig = 0;
+    double t_prev = 0.0;
+    int status = PF_ST_OK;     // the cluster's status: the same in every block
+    if (job.acc) {             // another trajectory of this row may already have rejected it
+        if (tid == 0 && rank == 0)
+            sh.cx_reject = *reinterpret_cast<volatile double *>(job.acc) < job.reject_below;
+        cl.sync();
+        if (*cl.map_shared_rank(&sh.cx_reject, 0)) status = PF_ST_REJECTED;
+    }
+    const unsigned long long Nl = static_cast<unsigned long long>(N);
+    for (int k = 0; k < K && status == PF_ST_OK; ++k) {
+        const uint32_t lane = (static_cast<uint32_t>(traj) << 20) | static_cast<uint32_t>(k);
+        if (k > 0) {
+            // systematic resampling over the whole population (the prefix sums
+            // of interval k-1 are global since barrier C)
+            const unsigned long long W = sh.cx_cum[C - 1];
+            if (tid == 0) {
+                const Philox4 w = philox4x32_10(0u, kResampleLane, lane, m32, key0, key1);
+                const unsigned long long r64 = (static_cast<unsigned long long>(w.w1) << 32) | w.w0;
+                sh.u_off = __umul64hi(r64, W);
+            }
+            __syncthreads();
+            const unsigned long long u_off = sh.u_off;
+            for (int jl = tid; jl < n; jl += B) {
+                const unsigned long long point =
+                    u_off + static_cast<unsigned long long>(j0 + jl) * W;
+                int r = 0;                      // the block holding a_j: first with N T_r > point
+                while (r < C - 1 && !(Nl * sh.cx_cum[r] > point)) ++r;
+                const unsigned long long *Qr = cl.map_shared_rank(qbuf, r);
+                int lo = 0, hi = min(Np, N - r * Np) - 1;   // a_j = min{i : N Q_i > point}
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (Nl * Qr[mid] > point) hi = mid; else lo = mid + 1;
+                }
+                const int a = r * Np + lo;
+                order[jl] = a;
+                if (want_digest) anc[jl] = a;
+                const int *xr = cl.map_shared_rank(xs, r);
+                for (int u = 0; u < U; ++u) stage[u * Np + jl] = xr[u * Np + lo];
+            }
+            cl.sync();   // D: no block reads another's prefix sums or states any more
+            for (int jl = tid; jl < n; jl += B)
+                for (int u = 0; u < U; ++u) xs[u * Np + jl] = stage[u * Np + jl];
+            __syncthreads();
+        } else if (want_digest) {
+            for (int jl = tid; jl < n; jl += B) anc[jl] = j0 + jl;
+        }
+
+        const double t_k = job.obs_times[k];
+        if (t_k > t_prev) {
+            if (tid == 0) {
+                sh.pool_next = 0;
+                sh.rem_n[0] = 0;
+                sh.rem_n[1] = 0;
+            }
+            for (int jl = tid; jl < n; jl += B) order[jl] = jl;
+            __syncthreads();
+            ssa_interval<RM, UM>(sh, xs, order, Np, n, t_prev, t_k, key0, key1, lane, m32,
+                                 job.budget, fired, static_cast<uint32_t>(j0));
+        }
+        __syncthreads();
+
+        if (want_digest)
+            for (int jl = tid; jl < n; jl += B)
+                dig += slot_digest_at(static_cast<uint32_t>(k), static_cast<uint32_t>(j0 + jl),
+                                      static_cast<uint32_t>(anc[jl]), xs, Np, U, jl);
+
+        const double *yk = job.y + static_cast<int64_t>(k) * P;
+        const bool svar = sh.net.obs_state_var != 0;
+        double lmax = -INFINITY;
+        for (int jl = tid; jl < n; jl += B) {
+            const double e = log_weight(sh, xs, Np, jl, yk, svar);
+            wbuf[jl] = e;
+            lmax = fmax(lmax, e);
+        }
+        const double bmax = block_max(lmax, sh);
+        if (tid == 0) {
+            sh.cx_lmax = bmax;
+            sh.cx_status = sh.status;
+        }
+        cl.sync();   // A
+        double emax = -INFINITY;
+        int st = PF_ST_OK;
+        for (int r = 0; r < C; ++r) {
+            emax = fmax(emax, *cl.map_shared_rank(&sh.cx_lmax, r));
+            const int sr = *cl.map_shared_rank(&sh.cx_status, r);
+            if (st == PF_ST_OK) st = sr;
+        }
+        if (st != PF_ST_OK) {
+            status = st;
+            break;
+        }
+        if (!isfinite(emax)) {
+            status = PF_ST_NONFINITE;
+            break;
+        }
+        double lsum = 0.0;
+        const double gmax = grid20(emax);
+        for (int jl = tid; jl < n; jl += B) {
+            const double e = wbuf[jl];
+            const double v = exp(__dsub_rn(e, emax));
+            lsum = __dadd_rn(lsum, v);
+            const double vq = svar ? exp(__dsub_rn(grid20(e), gmax)) : v;
+            qbuf[jl] = __double2ull_rz(__dmul_rn(vq, 4294967296.0));
+        }
+        const double bsum = block_sum(lsum, sh);
+        block_scan_u64(qbuf, n, sh);
+        if (tid == 0) {
+            sh.cx_lsum = bsum;
+            sh.cx_qtot = qbuf[n - 1];
+        }
+        cl.sync();   // B
+        if (tid == 0) {
+            double s = 0.0;
+            unsigned long long run = 0;
+            for (int r = 0; r < C; ++r) {
+                s = __dadd_rn(s, *cl.map_shared_rank(&sh.cx_lsum, r));
+                run += *cl.map_shared_rank(&sh.cx_qtot, r);
+                sh.cx_cum[r] = run;
+            }
+            if (rank == 0) {
+                double inc = __dadd_rn(emax, log(s));
+                inc = __dsub_rn(inc, log(static_cast<double>(N)));
+                inc = __dsub_rn(inc, sh.lognorm);
+                sh.ll = __dadd_rn(sh.ll, inc);
+                sh.cx_reject = 0;
+                if (job.acc) {
+                    const double add = __dsub_rn(inc, job.slack);
+                    sh.cx_reject = __dadd_rn(atomicAdd(job.acc, add), add) < job.reject_below;
+                }
+            }
+        }
+        __syncthreads();
+        const unsigned long long off = rank > 0 ? sh.cx_cum[rank - 1] : 0ull;
+        for (int jl = tid; jl < n; jl += B) qbuf[jl] += off;
+        cl.sync();   // C
+        if (*cl.map_shared_rank(&sh.cx_reject, 0)) status = PF_ST_REJECTED;
+        t_prev = t_k;
+    }
+    __syncthreads();
+    const unsigned long long fired_b = block_sum_u64(fired, sh);
+    const unsigned long long dig_b = want_digest ? block_sum_u64(dig, sh) : 0ull;
+    if (tid == 0) {
+        sh.cx_fired = fired_b;
+        sh.cx_dig = dig_b;
+    }
+    cl.sync();   // E
+    if (tid == 0 && rank == 0) {
+        unsigned long long fired_all = 0, dig_all = 0;
+        for (int r = 0; r < C; ++r) {
+            fired_all += *cl.map_shared_rank(&sh.cx_fired, r);
+            dig_all += *cl.map_shared_rank(&sh.cx_dig, r);
+        }
+        *job.ll_out = status == PF_ST_OK ? sh.ll : -INFINITY;
+        *job.st_out = static_cast<uint8_t>(status);
+        *job.ev_out = fired_all;
+        if (job.dg_out) *job.dg_out = dig_all;
+    }
+    if (job.fs_out && status == PF_ST_OK) {
+        for (int jl = tid; jl < n; jl += B)
+            for (int u = 0; u < U; ++u)
+                job.fs_out[static_cast<int64_t>(j0 + jl) * U + u] = xs[u * Np + jl];
+    }
+    cl.sync();   // F: no block leaves while block 0 still reads the others' slots
 }
 
 }  // namespace dev

@@ -77,6 +77,49 @@ __global__ void __launch_bounds__(128, 4) filter_kernel(const FilterArgs args) {
     run_filter<RM, UM>(job, sh, smem);
 }
 
+// A filter split over the C blocks of a thread-block cluster (cluster size
+// set at launch): cluster c runs filter slot c, its blocks on C SMs.
+template <int RM, int UM>
+__global__ void __launch_bounds__(128, 4) filter_kernel_cluster(const FilterArgs args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SharedHead sh;
+    const int tid = threadIdx.x, B = blockDim.x;
+    const int T = args.T;
+    const int64_t slot = blockIdx.x / cooperative_groups::this_cluster().num_blocks();
+    int64_t mrow = slot / T;
+    const int traj = static_cast<int>(slot - mrow * T);
+    if (args.row_order) mrow = args.row_order[mrow];
+    const int64_t f = mrow * T + traj;
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&args.net);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&sh.net);
+        for (int i = tid; i < static_cast<int>(sizeof(NetTables) / 4); i += B) dst[i] = src[i];
+    }
+    load_zig_table(sh.zig, args.zig);
+    if (tid == 0) sh.zig_g = args.zig;
+    __syncthreads();
+    FilterJob job;
+    job.theta = args.thetas + mrow * args.net.d;
+    job.obs_times = args.obs_times;
+    job.y = args.y + static_cast<int64_t>(traj) * args.K * args.net.P;
+    job.K = args.K;
+    job.N = args.N;
+    job.mrow = static_cast<uint32_t>(mrow);
+    job.traj = traj;
+    job.seed = args.seed;
+    job.budget = args.budget;
+    job.ll_out = args.ll_f + f;
+    job.st_out = args.st_f + f;
+    job.ev_out = reinterpret_cast<unsigned long long *>(args.ev_f) + f;
+    job.dg_out = args.dg_f ? reinterpret_cast<unsigned long long *>(args.dg_f) + f : nullptr;
+    job.fs_out = args.final_states ? args.final_states + f * static_cast<int64_t>(args.N) * args.net.U
+                                   : nullptr;
+    job.acc = args.acc ? args.acc + mrow : nullptr;
+    job.reject_below = args.reject_below;
+    job.slack = args.slack;
+    run_filter_cluster<RM, UM>(job, sh, smem);
+}
+
 // Populations too large for shared memory: a grid of resident blocks walks
 // the filters (grid stride), each block keeping its population in its own slab
 // of global memory (N (16 + 8U) bytes), which stays in L1/L2 while it runs.
@@ -279,7 +322,34 @@ int launch_tier(const FilterArgs &a, int B, size_t smem, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+template <int RM, int UM>
+int launch_tier_cluster(const FilterArgs &a, int B, size_t smem, int C, cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(filter_kernel_cluster<RM, UM>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(static_cast<unsigned>(a.M * a.T * C));
+    cfg.blockDim = dim3(static_cast<unsigned>(B));
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = static_cast<unsigned>(C);
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, filter_kernel_cluster<RM, UM>, a);
+    if (e != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t cluster_smem_bytes(int N, int C, int U, bool digest) {
+    return cluster_share_bytes(N, C, U, digest);
+}
 
 size_t filter_smem_bytes(int N, int U, bool digest) {
     return static_cast<size_t>(N) * (8 + 4 * static_cast<size_t>(U) + 4 + (digest ? 4 : 0)) + 16;
@@ -311,6 +381,17 @@ int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, v
                                 : launch_tier_global<8, 0>(a, B, slabs, slab_bytes, grid, s); break;
             case 16: e = launch_tier_global<16, 0>(a, B, slabs, slab_bytes, grid, s); break;
             default: e = launch_tier_global<32, 0>(a, B, slabs, slab_bytes, grid, s); break;
+        }
+    } else if (a.cluster > 1) {
+        const int C = a.cluster;
+        const size_t cs = cluster_smem_bytes(a.N, C, a.net.U, a.dg_f != nullptr);
+        switch (reaction_tier(a.net.R)) {
+            case 4: e = small_u ? launch_tier_cluster<4, 4>(a, B, cs, C, s)
+                                : launch_tier_cluster<4, 0>(a, B, cs, C, s); break;
+            case 8: e = small_u ? launch_tier_cluster<8, 4>(a, B, cs, C, s)
+                                : launch_tier_cluster<8, 0>(a, B, cs, C, s); break;
+            case 16: e = launch_tier_cluster<16, 0>(a, B, cs, C, s); break;
+            default: e = launch_tier_cluster<32, 0>(a, B, cs, C, s); break;
         }
     } else switch (reaction_tier(a.net.R)) {
         case 4: e = small_u ? launch_tier<4, 4>(a, B, smem, s) : launch_tier<4, 0>(a, B, smem, s); break;

@@ -62,11 +62,15 @@ struct FilterArgs {
     double reject_below;
     double slack;               // upper bound of one per-time-point log increment, >= 0
     const ZigTab *zig;          // device copy of the exponential ziggurat table
+    int32_t cluster;            // > 1: each filter split over a cluster of this many blocks
 };
 
 // Bytes of the particle population of one filter: N (8 + 4U + 4) bytes, plus
 // 4N for the ancestors when the digest is requested.
 size_t filter_smem_bytes(int N, int U, bool digest);
+
+// Bytes of one block's share of a filter split over a cluster of C blocks.
+size_t cluster_smem_bytes(int N, int C, int U, bool digest);
 
 // Largest reaction-count template that fits R.
 int reaction_tier(int R);

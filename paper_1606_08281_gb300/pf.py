@@ -25,6 +25,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT, PF_EAGAIN, PF_ENOTFOUND, PF_
     0, -1, -2, -3, -4, -5, -6, -7)
 PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA, PF_ST_REJECTED = 0, 1, 2, 3, 4
 PF_SCHED_AUTO, PF_SCHED_NATURAL, PF_SCHED_HEAVY_FIRST = 0, 1, 2
+PF_MAX_CLUSTER_BLOCKS = 8
 
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",
@@ -64,7 +65,8 @@ class pf_options(ct.Structure):
                 ("ll_traj", ct.c_void_p), ("events", ct.c_void_p), ("digest", ct.c_void_p),
                 ("final_states", ct.c_void_p), ("schedule", ct.c_int32),
                 ("early_reject", ct.c_int32), ("row_order", ct.c_void_p),
-                ("reject_below", ct.c_double), ("model", ct.POINTER(pf_model))]
+                ("reject_below", ct.c_double), ("model", ct.POINTER(pf_model)),
+                ("cluster_blocks", ct.c_int32)]
 
 
 class pf_fsp_options(ct.Structure):
@@ -217,11 +219,13 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
               event_budget: int = 0, block_threads: int = 0, stream=None,
               diagnostics: bool = False, final_states: bool = False, out=None,
               schedule: int = PF_SCHED_AUTO, row_order=None, reject_below=None,
-              model: dict | None = None):
+              model: dict | None = None, cluster_blocks: int = 0):
     """Log-likelihood of every theta row (see pf_loglik in include/pf1606.h).
 
     model: optional Lac-Gfp extensions {"rate_coef", "x0_hi", "obs_offset",
     "obs_var"} (pf_model; host arrays).
+    cluster_blocks: 2..8 splits each filter over a thread-block cluster of
+    that many blocks (pf_options.cluster_blocks); 0 = one block per filter.
 
     Returns a dict with 'loglik' [M] and 'status' [M]; with diagnostics=True
     also 'll_traj', 'events', 'digest' [M][T]; with final_states=True also
@@ -288,7 +292,8 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
     opt = pf_options(int(event_budget), 1 if device else 0, int(block_threads),
                      stream if device else None, ptr("ll_traj"), ptr("events"), ptr("digest"),
                      ptr("final_states"), int(schedule), 0 if reject_below is None else 1, p_ro,
-                     float("nan") if reject_below is None else float(reject_below), mdl.ptr())
+                     float("nan") if reject_below is None else float(reject_below), mdl.ptr(),
+                     int(cluster_blocks))
     rc = lib.pf_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), p_ts, K, p_y, T, P, _hptr(Ch),
                        _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
                        ptr("loglik"), ptr("status"), ct.byref(opt))
