@@ -53,3 +53,34 @@ def test_binding_names_match_the_header():
     from paper_1606_08281_gb300 import pf
     for name in declared_functions():
         assert hasattr(pf, name), name
+
+
+STRUCTS = ["pf_network", "pf_model", "pf_options", "pf_fsp_options", "pf_ode_options",
+           "pf_request"]
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes struct of the binding has the C struct's size and field
+    offsets (the header compiled by the host C compiler), so that an option
+    added on one side only cannot shift the others."""
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    from paper_1606_08281_gb300 import pf
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "pf1606.h"', "int main(void) {"]
+    for name in STRUCTS:
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for fname, _ in getattr(pf, name)._fields_:
+            lines.append(f'printf("{name} {fname} %zu\\n", offsetof({name}, {fname}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", str(ROOT / "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    c_side = {tuple(line.split()[:2]): int(line.split()[2]) for line in out.splitlines()}
+    for name in STRUCTS:
+        cls = getattr(pf, name)
+        assert c_side[(name, "size")] == ct.sizeof(cls), name
+        for fname, _ in cls._fields_:
+            assert c_side[(name, fname)] == getattr(cls, fname).offset, (name, fname)
