@@ -303,7 +303,7 @@ int pf_fsp_loglik(const pf_network *net, const double *thetas, int64_t M, int32_
 typedef struct {
     int32_t device_ptrs;   /* 1: thetas, y, loglik, status, ll_pattern, steps are device pointers */
     void *stream;          /* cudaStream_t (NULL = legacy default stream) */
-    double rtol, atol;     /* 0 = defaults 1e-10, 1e-13 */
+    double rtol, atol;     /* 0 = defaults 1e-10, 1e-13; negative: PF_EINVAL */
     int32_t max_steps;     /* per pattern (accepted + rejected); 0 = default 200000 */
     double *ll_pattern;    /* optional [M][n_patterns] per-pattern values */
     uint32_t *steps;       /* optional [M][n_patterns] steps taken */

@@ -243,11 +243,13 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     if (rc) return rc;
     rc = check_count_range(a.net, K, budget);
     if (rc) return rc;
-    {
-        int ze = 0;
-        a.zig = pf::zig_table_device(&ze);
-        if (!a.zig) return cuda_fail(ze, "ziggurat table");
+    // observation times (always a host array): strictly increasing, >= 0, finite
+    for (int k = 0; k < K; ++k) {
+        const bool bad = !std::isfinite(obs_times[k]) ||
+                         (k == 0 ? obs_times[k] < 0.0 : !(obs_times[k] > obs_times[k - 1]));
+        if (bad) return fail(PF_EINVAL, "obs_times must be finite, >= 0 and strictly increasing (index %d)", k);
     }
+    // launch shape (checked, like everything above, before any device call)
     const int CB = o.cluster_blocks;
     if (CB < 0 || CB > PF_MAX_CLUSTER_BLOCKS)
         return fail(PF_EINVAL, "cluster_blocks %d outside 0..%d", CB, PF_MAX_CLUSTER_BLOCKS);
@@ -257,6 +259,11 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     int B = o.block_threads;
     if (B == 0) B = std::min(128, ((Nb + 31) / 32) * 32);
     if (B < 32 || B > 128 || (B % 32)) return fail(PF_EINVAL, "block_threads %d must be a multiple of 32 in 32..128", B);
+    {
+        int ze = 0;
+        a.zig = pf::zig_table_device(&ze);
+        if (!a.zig) return cuda_fail(ze, "ziggurat table");
+    }
     const size_t smem = pf::filter_smem_bytes(N, a.net.U, o.digest != nullptr);
     int dev = 0, smem_max = 0, sms = 0;
     PF_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
@@ -273,12 +280,6 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     }
 
     cudaStream_t s = static_cast<cudaStream_t>(o.stream);
-    // observation times (always a host array): strictly increasing, >= 0, finite
-    for (int k = 0; k < K; ++k) {
-        const bool bad = !std::isfinite(obs_times[k]) ||
-                         (k == 0 ? obs_times[k] < 0.0 : !(obs_times[k] > obs_times[k - 1]));
-        if (bad) return fail(PF_EINVAL, "obs_times must be finite, >= 0 and strictly increasing (index %d)", k);
-    }
     if (M == 0) return PF_OK;
 
     const int64_t F = M * T;

@@ -360,6 +360,7 @@ extern "C" int pf_erk_loglik(const double *thetas, int64_t M, const double *swit
                 return fail(PF_EINVAL, "switch times of pattern %d must increase", p);
         }
     }
+    if (!(o.rtol >= 0.0) || !(o.atol >= 0.0)) return fail(PF_EINVAL, "rtol and atol must be >= 0 (0 = default)");
     const double rtol = o.rtol > 0.0 ? o.rtol : 1e-10, atol = o.atol > 0.0 ? o.atol : 1e-13;
     if (!(rtol >= 1e-14 && rtol < 1.0) || !(atol > 0.0)) return fail(PF_EINVAL, "rtol in [1e-14, 1), atol > 0");
     const int max_steps = o.max_steps > 0 ? o.max_steps : 200000;

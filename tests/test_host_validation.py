@@ -1,0 +1,73 @@
+"""Argument checks of the C ABI that run on the host before any device call
+(CPU only): each malformed call returns PF_EINVAL with a message, so a caller
+learns of the mistake without a GPU and without a launch."""
+from __future__ import annotations
+
+import shutil
+from pathlib import Path
+
+import numpy as np
+import pytest
+
+from paper_1606_08281_gb300 import workloads as W
+
+
+@pytest.fixture(scope="module")
+def pf():
+    if shutil.which("nvcc") is None and not Path("/usr/local/cuda/bin/nvcc").exists():
+        pytest.skip("nvcc not available")
+    from paper_1606_08281_gb300 import build, pf as pfmod
+    build.build()
+    pfmod.load()
+    return pfmod
+
+
+def einval(pf, fn, *args, **kw):
+    with pytest.raises(pf.PfError) as e:
+        fn(*args, **kw)
+    assert e.value.code == pf.PF_EINVAL, e.value
+    return str(e.value)
+
+
+def test_filter_arguments(pf):
+    w = W.gene_expression().subset(T=2, K=6)
+    th, y = w.thetas(3), w.observations()
+    call = lambda **kw: pf.pf_loglik(  # noqa: E731
+        kw.pop("net", w.net), kw.pop("th", th), w.x0, kw.pop("times", w.obs_times), kw.pop("y", y),
+        w.C, kw.pop("sigma", w.sigma), kw.pop("N", 100), 1, **kw)
+    assert "n_particles" in einval(pf, call, N=0)
+    einval(pf, call, N=pf.PF_MAX_PARTICLES + 1 if hasattr(pf, "PF_MAX_PARTICLES") else 16385)
+    assert "obs_times" in einval(pf, call, times=w.obs_times[::-1].copy())
+    einval(pf, call, times=np.array([0.0, 1.0, 1.0, 2.0, 3.0, 4.0]))      # not strictly increasing
+    einval(pf, call, times=np.array([-1.0, 1.0, 2.0, 3.0, 4.0, 5.0]))     # negative
+    einval(pf, call, sigma=np.array([0.0]))
+    einval(pf, call, event_budget=1 << 33)
+    assert "block_threads" in einval(pf, call, block_threads=48)
+    einval(pf, call, block_threads=256)
+    einval(pf, call, net={"reactants": [[3, 0]], "products": [[0, 0]], "rate_index": None},
+           th=np.ones((3, 1)))                                             # order 3 in one species
+
+
+def test_cluster_arguments(pf):
+    w = W.birth_death()
+    call = lambda cb, N=64: pf.pf_loglik(  # noqa: E731
+        w.net, w.thetas(2), w.x0, w.obs_times, w.observations(), w.C, w.sigma, N, 5,
+        cluster_blocks=cb)
+    assert "cluster_blocks" in einval(pf, call, -1)
+    einval(pf, call, pf.PF_MAX_CLUSTER_BLOCKS + 1)
+    # ceil(N / C) per block must leave the last block at least one particle
+    for N, cb in [(6, 5), (9, 8), (2, 3), (1, 2)]:
+        assert "empty" in einval(pf, call, cb, N)
+
+
+def test_fsp_and_ode_arguments(pf):
+    t = W.telegraph()
+    einval(pf, pf.pf_fsp_loglik, t.net, t.thetas(2), t.x0, [1, 1, 5000], t.obs_times,
+           t.observations(), t.C, t.sigma)                                  # box too large
+    einval(pf, pf.pf_fsp_loglik, t.net, t.thetas(2), t.x0, [1, 1, -1], t.obs_times,
+           t.observations(), t.C, t.sigma)
+    e = W.erk()
+    y = e.observations()
+    einval(pf, pf.pf_erk_loglik, e.thetas(2), e.patterns, np.r_[0.0, e.obs_times[1:]], y)
+    einval(pf, pf.pf_erk_loglik, e.thetas(2), e.patterns, e.obs_times, y, rtol=2.0)
+    einval(pf, pf.pf_erk_loglik, e.thetas(2), e.patterns, e.obs_times, y, rtol=1e-10, atol=-1.0)
