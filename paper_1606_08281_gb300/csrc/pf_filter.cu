@@ -2,7 +2,8 @@
 //
 // One thread block runs one filter, i.e. one (theta row, observed trajectory)
 // pair, through all K observation times (Supp. I, algorithm "Likelihood
-// Approximation using particle filter"):
+// Approximation using particle filter"); on request the filter is split over
+// the blocks of a thread-block cluster instead (filter_kernel_cluster):
 //   resample by the previous weights -> simulate every particle to t_k with
 //   the direct-method SSA -> Gaussian weight -> log-sum-exp increment.
 // Within one interval the particles form a pool: each lane simulates one
