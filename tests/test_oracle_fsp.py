@@ -135,6 +135,40 @@ def test_gene_expression_filter_unbiased_against_fsp(S=300):
         assert lls.mean() <= L + 4 * lls.std(ddof=1) / np.sqrt(S)
 
 
+# A network of the cascade's kind small enough for an exact likelihood: three
+# species, reactions of order 0, 1 and 2 (a heterodimer A + B and a homodimer
+# B + B), two reactions sharing one rate column, two observed species.
+THREE = {"reactants": np.array([[0, 0, 0], [1, 0, 0], [1, 1, 0], [0, 2, 0], [0, 0, 1], [0, 0, 1]],
+                               np.int32),
+         "products": np.array([[1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, 0], [0, 0, 0], [1, 0, 0]],
+                              np.int32),
+         "rate_index": np.array([0, 1, 2, 3, 4, 4], np.int32)}
+
+
+def test_second_order_network_filter_unbiased_against_fsp(S=300):
+    """The filter oracle on THREE (the features of the 10-species cascade,
+    whose own likelihood has no FSP box): on the box 0..25^3 the FSP
+    likelihood loses < 1e-10 of the mass, and mean exp(ll_PF - L_FSP) = 1 at
+    the data-generating theta and at a perturbed one; Jensen for the mean of
+    ll."""
+    th_star = np.array([2.0, 0.6, 0.15, 0.1, 0.25])
+    x0 = np.array([2, 1, 0], np.int32)
+    times = np.arange(1.0, 7.0)
+    C = np.array([[1.0, 0.0, 0.0], [0.0, 0.0, 1.0]])
+    sigma = np.array([1.0, 1.5])
+    path, _, _ = pf_oracle.ssa_paths(THREE, th_star, x0, times, 1, seed=5)
+    y = (path[0] @ C.T + np.random.default_rng(9).normal(size=(len(times), 2)) * sigma)[None]
+    for th in [th_star, th_star * np.array([1.5, 0.7, 1.0, 2.0, 0.8])]:
+        L, leak = fsp.loglik(THREE, th, x0, [25, 25, 25], times, y[0], C, sigma)
+        assert abs(leak) < 1e-10
+        lls = np.array([pf_oracle.pf_loglik(THREE, [th], x0, times, y, C, sigma, 200,
+                                            900 + s)["loglik"][0] for s in range(S)])
+        z = np.exp(lls - L)
+        se = z.std(ddof=1) / np.sqrt(S)
+        assert abs(z.mean() - 1.0) < 4 * se + 1e-3, (th, z.mean(), se)
+        assert lls.mean() <= L + 4 * lls.std(ddof=1) / np.sqrt(S)
+
+
 # ------------------------------------------------------------- mutants ----
 MUTANTS = {
     "propagate_transposed": ("splinalg.expm_multiply(Q.T.tocsc() * dt, alpha)",
