@@ -2,7 +2,6 @@
 values computed with 40-digit decimal arithmetic."""
 from __future__ import annotations
 
-import math
 from decimal import Decimal, getcontext
 
 import numpy as np
