@@ -412,7 +412,7 @@ def main() -> None:
             "metric": "theta-likelihoods/s", "value": value, "unit": "theta-likelihoods/s",
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {**config_of(w), "launch": launch},
+            "data": "synthetic", "config": config_of(w), "launch": launch,
             "ssa_events_per_s": world * ev_step / (ms * 1e-3),
             "events_per_step": ev_step, "budget_rows": budget_rows,
             "clocks": clk,

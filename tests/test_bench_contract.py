@@ -1,0 +1,33 @@
+"""bench.py's reference arm (the oracle on the host cores) prints one JSON line
+with the contract's keys and the same metric, unit and workload config as the
+GPU arm (CPU only: the small birth-death workload, about 20 s)."""
+from __future__ import annotations
+
+import json
+import subprocess
+import sys
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def test_reference_arm_line():
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                          "birth_death", "--steps", "1", "--warmup", "0"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=300, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, out
+    line = json.loads(lines[0])
+    sys.path.insert(0, str(ROOT))
+    import bench
+    from paper_1606_08281_gb300 import workloads as W
+    assert line["impl"] == "reference"
+    assert line["metric"] == "theta-likelihoods/s" and line["unit"] == "theta-likelihoods/s"
+    assert line["higher_is_better"] is True and line["steps"] == 1 and line["warmup"] == 0
+    assert line["config"] == bench.config_of(W.get("birth_death"))
+    assert line["value"] > 0 and line["ms_per_step"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
