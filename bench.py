@@ -165,40 +165,47 @@ def _oracle_row(args):
     return int(r["events"][r["status"] == 0].sum())
 
 
-def oracle_baseline(name: str, seconds: float) -> dict:
-    """The oracle as it stands, one single-threaded process per host core
-    (spawned, warmed up before the clock starts), taking theta rows in row
-    order; rows finished within the wall-time window are counted and the pool
-    is terminated at its end, so a row that would run for long cannot hold the
-    leg past the window."""
+def _windowed(warm, warm_arg, row, tasks, seconds: float):
+    """Run `row` over `tasks` on one spawned single-threaded process per host
+    core (each warmed up by `warm` before the clock starts) and count the rows
+    finished within the wall-time window; the pool is terminated at its end,
+    so a row that would run for long cannot hold the leg past the window.
+    Returns (rows finished, sum of their row values, wall seconds, cores)."""
     import multiprocessing as mp
     cores = os.cpu_count() or 1
-    w = W.get(name)
     ctx = mp.get_context("spawn")
     pool = ctx.Pool(cores)
-    done, events = 0, 0
+    done, total = 0, 0
     try:
-        pool.map(_oracle_warm, [name] * cores, chunksize=1)
+        pool.map(warm, [warm_arg] * cores, chunksize=1)
         t0 = time.time()
         deadline = t0 + seconds
-        # rows in order, starting over when a short batch is exhausted before the window ends
-        n_tasks = max(w.M, 50_000)
-        it = pool.imap_unordered(_oracle_row, [(name, m % w.M) for m in range(n_tasks)],
-                                 chunksize=1)
+        it = pool.imap_unordered(row, tasks, chunksize=1)
         while True:
             remaining = deadline - time.time()
             if remaining <= 0:
                 break
             try:
-                ev = it.next(timeout=remaining)
+                v = it.next(timeout=remaining)
             except (mp.TimeoutError, StopIteration):
                 break
             done += 1
-            events += ev
+            total += v
         wall = time.time() - t0
     finally:
         pool.terminate()
         pool.join()
+    return done, total, wall, cores
+
+
+def oracle_baseline(name: str, seconds: float) -> dict:
+    """The filter oracle as it stands, one single-threaded process per host
+    core, taking theta rows in row order (starting over when a short batch is
+    exhausted before the window ends)."""
+    w = W.get(name)
+    n_tasks = max(w.M, 50_000)
+    done, events, wall, cores = _windowed(_oracle_warm, name, _oracle_row,
+                                          [(name, m % w.M) for m in range(n_tasks)], seconds)
     return {
         "value": done / wall if wall > 0 else 0.0,
         "unit": "theta-likelihoods/s",
@@ -209,6 +216,56 @@ def oracle_baseline(name: str, seconds: float) -> dict:
                    f"the {name} batch, taken in row order (cycling) by {cores} single-threaded "
                    f"oracle processes; rate = rows finished / wall time of the {wall:.1f} s "
                    f"window"),
+        "wall_s": wall,
+    }
+
+
+def _exact_warm(key):
+    """Worker start-up for the FSP / ODE oracle legs: key = (leg, workload, M)."""
+    sys.path.insert(0, str(ROOT))
+    if key not in _ORACLE_CACHE:
+        leg, name, M = key
+        if leg == "ode":
+            from oracle import ode as mod
+            w = W.erk()
+            w.M = M
+        else:
+            from oracle import fsp as mod
+            w = W.get(name)
+        _ORACLE_CACHE[key] = (mod, w, w.thetas(), w.observations())
+    return os.getpid()
+
+
+def _exact_row(args):
+    """Worker: the FSP or ODE oracle's log-likelihood of one theta row."""
+    key, m = args
+    _exact_warm(key)
+    mod, w, th, y = _ORACLE_CACHE[key]
+    if key[0] == "ode":
+        mod.loglik(th[m], w.patterns, w.obs_times, y)
+    else:
+        for t in range(w.T):
+            mod.loglik(w.net, th[m], w.x0, w.fsp_box, w.obs_times, y[t], w.C, w.sigma, w.model)
+    return 0
+
+
+def exact_baseline(leg: str, name: str, M: int, seconds: float) -> dict:
+    """The FSP (scipy expm_multiply) or ODE (scipy DOP853, rtol 1e-11) oracle
+    as it stands on the same theta batch, one single-threaded process per host
+    core, rows in row order."""
+    key = (leg, name, M)
+    done, _, wall, cores = _windowed(_exact_warm, key, _exact_row,
+                                     [(key, m) for m in range(M)], seconds)
+    what = ("ODE oracle (scipy DOP853, rtol 1e-11)" if leg == "ode"
+            else "FSP oracle (scipy expm_multiply)")
+    return {
+        "value": done / wall if wall > 0 else 0.0,
+        "unit": "theta-likelihoods/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": (f"{done} theta rows of the {M}-row {name} batch, in row order, by {cores} "
+                   f"single-threaded {what} processes; rate = rows finished / wall time of the "
+                   f"{wall:.1f} s window"),
         "wall_s": wall,
     }
 
@@ -544,7 +601,9 @@ def run_fsp(a, pf) -> None:
                          "unit": "T FP64 ops/s", "frac": ops_rate / peak_ops, "traffic": None,
                          "kernel": "fsp_kernel (FP64 pipe; the probability vectors stay in "
                                    "shared memory)",
-                         "fp64_ops_per_step": ops}}
+                         "fp64_ops_per_step": ops},
+            "cpu_baseline": (None if a.no_cpu_baseline
+                             else exact_baseline("fsp", w.name, w.M, a.cpu_seconds))}
     print(json.dumps(line), flush=True)
 
 
@@ -605,7 +664,9 @@ def run_ode(a, pf) -> None:
             "roofline": {"bound": "alu", "achieved": ops_rate / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP64 ops/s", "frac": ops_rate / peak_ops, "traffic": None,
                          "kernel": "erk_kernel (FP64 pipe; a lane pair per theta and pattern)",
-                         "fp64_ops_per_dp_step": ODE_OPS_PER_STEP}}
+                         "fp64_ops_per_dp_step": ODE_OPS_PER_STEP},
+            "cpu_baseline": (None if a.no_cpu_baseline
+                             else exact_baseline("ode", "erk", w.M, a.cpu_seconds))}
     print(json.dumps(line), flush=True)
 
 

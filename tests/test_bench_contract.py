@@ -31,3 +31,15 @@ def test_reference_arm_line():
     e2e = line["e2e"]
     assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_exact_oracle_legs():
+    """The FSP and ODE oracle legs of `bench.py --mode fsp / ode` count rows
+    finished in a short window (a few seconds of host work each)."""
+    sys.path.insert(0, str(ROOT))
+    import bench
+    for leg, name, M in [("fsp", "telegraph", 64), ("ode", "erk", 64)]:
+        r = bench.exact_baseline(leg, name, M, 3.0)
+        assert r["kind"] == "oracle" and r["cores"] >= 1 and r["unit"] == "theta-likelihoods/s"
+        assert r["value"] > 0 and r["wall_s"] <= 10.0, r
+        assert f"{M}-row {name} batch" in r["sample"]
