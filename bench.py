@@ -270,8 +270,39 @@ def exact_baseline(leg: str, name: str, M: int, seconds: float) -> dict:
     }
 
 
+def run_reference_exact(a) -> None:
+    """The reference arm of --mode fsp / ode: the FSP or ODE oracle as it
+    stands on the GPU arm's theta batch, each step a bounded window."""
+    if a.mode == "fsp":
+        w = fsp_workload(a.workload)
+        leg, name, metric, config = "fsp", w.name, "exact FSP theta-likelihoods/s", fsp_config(w)
+    else:
+        w = ode_workload(a.ode_theta)
+        leg, name, metric, config = "ode", "erk", "ODE theta-likelihoods/s", ode_config(w)
+    per_step = max(5.0, min(30.0, 150.0 / max(1, a.steps + a.warmup)))
+    for _ in range(a.warmup):
+        exact_baseline(leg, name, w.M, per_step / 4)
+    vals, last = [], None
+    for _ in range(a.steps):
+        last = exact_baseline(leg, name, w.M, per_step)
+        vals.append(last["value"])
+    value = float(np.mean(vals))
+    print(json.dumps({
+        "impl": "reference", "metric": metric, "mode": a.mode, "value": value,
+        "unit": "theta-likelihoods/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": 1e3 * w.M / value if value > 0 else None, "higher_is_better": True,
+        "dtype": "f64", "data": "synthetic", "config": config,
+        "cpu_baseline": {k: last[k] for k in ("kind", "cores", "sample")} | {"value": value,
+                                                                           "unit": last["unit"]},
+        "e2e": {"value": value, "unit": "theta-likelihoods/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}), flush=True)
+
+
 def run_reference(a, rank: int) -> None:
     if rank != 0:
+        return
+    if a.mode in ("fsp", "ode"):
+        run_reference_exact(a)
         return
     w = W.get(a.workload)
     per_step = max(5.0, min(30.0, 150.0 / max(1, a.steps + a.warmup)))
@@ -297,6 +328,29 @@ def run_reference(a, rank: int) -> None:
         "ssa_events_per_s": last["ssa_events_per_s"],
     }
     print(json.dumps(line), flush=True)
+
+
+def fsp_workload(name: str):
+    """The FSP mode's workload: telegraph or birth_death (the others have no box)."""
+    return W.get(name if name in ("telegraph", "birth_death") else "telegraph")
+
+
+def fsp_config(w) -> dict:
+    return {"workload": f"{w.name}: FSP box {list(map(int, w.fsp_box))}, K={w.K} T={w.T} M={w.M}",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+def ode_workload(M: int):
+    w = W.erk()
+    w.M = M
+    return w
+
+
+def ode_config(w) -> dict:
+    return {"workload": f"erk: {w.M} theta (within a factor e of theta_bar) x "
+                        f"{len(w.patterns)} input patterns x {w.K} FRET readings",
+            "rtol": 1e-10, "atol": 1e-13,
+            "l2": "flushed between timed steps (256 MiB write)"}
 
 
 def config_of(w) -> dict:
@@ -557,7 +611,7 @@ def fsp_ops(w, th) -> float:
 def run_fsp(a, pf) -> None:
     """The exact FSP likelihood of every theta row of a workload (one JSON line)."""
     import torch
-    w = W.get(a.workload if a.workload in ("telegraph", "birth_death") else "telegraph")
+    w = fsp_workload(a.workload)
     th_np = w.thetas()
     dev = torch.device("cuda", torch.cuda.current_device())
     th = torch.from_numpy(th_np).to(dev)
@@ -593,9 +647,7 @@ def run_fsp(a, pf) -> None:
     line = {"metric": "exact FSP theta-likelihoods/s", "mode": "fsp", "value": w.M / (ms * 1e-3),
             "unit": "theta-likelihoods/s", "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
             "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"{w.name}: FSP box {list(map(int, w.fsp_box))}, "
-                                   f"K={w.K} T={w.T} M={w.M}",
-                       "l2": "flushed between timed steps (256 MiB write)"},
+            "config": fsp_config(w),
             "clocks": clk,
             "roofline": {"bound": "alu", "achieved": ops_rate / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP64 ops/s", "frac": ops_rate / peak_ops, "traffic": None,
@@ -619,8 +671,7 @@ ODE_OPS_PER_STEP = 6 * 160 + 14 * 27 + 14 * 20
 def run_ode(a, pf) -> None:
     """The Erk-model likelihood of every theta row (one JSON line)."""
     import torch
-    w = W.erk()
-    w.M = a.ode_theta
+    w = ode_workload(a.ode_theta)
     dev = torch.device("cuda", torch.cuda.current_device())
     th = torch.from_numpy(w.thetas()).to(dev)
     yd = torch.from_numpy(w.observations()).to(dev)
@@ -656,10 +707,7 @@ def run_ode(a, pf) -> None:
     line = {"metric": "ODE theta-likelihoods/s", "mode": "ode", "value": w.M / (ms * 1e-3),
             "unit": "theta-likelihoods/s", "n_gpus": 1, "steps": a.steps, "warmup": max(3, a.warmup),
             "ms_per_step": ms, "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"erk: {w.M} theta (within a factor e of theta_bar) x "
-                                   f"{len(w.patterns)} input patterns x {w.K} FRET readings",
-                       "rtol": 1e-10, "atol": 1e-13,
-                       "l2": "flushed between timed steps (256 MiB write)"},
+            "config": ode_config(w),
             "dp_steps_per_launch": steps, "clocks": clk,
             "roofline": {"bound": "alu", "achieved": ops_rate / 1e12, "peak": peak_ops / 1e12,
                          "unit": "T FP64 ops/s", "frac": ops_rate / peak_ops, "traffic": None,

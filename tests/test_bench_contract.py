@@ -43,3 +43,19 @@ def test_exact_oracle_legs():
         assert r["kind"] == "oracle" and r["cores"] >= 1 and r["unit"] == "theta-likelihoods/s"
         assert r["value"] > 0 and r["wall_s"] <= 10.0, r
         assert f"{M}-row {name} batch" in r["sample"]
+
+
+def test_reference_arm_of_the_ode_mode():
+    """--mode ode --impl reference times the ODE oracle on the GPU arm's batch
+    and config (64 rows: a few seconds)."""
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--mode", "ode",
+                          "--ode-theta", "64", "--steps", "1", "--warmup", "0"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=300, check=True).stdout
+    line = json.loads([ln for ln in out.splitlines() if ln.startswith("{")][-1])
+    sys.path.insert(0, str(ROOT))
+    import bench
+    assert line["impl"] == "reference" and line["mode"] == "ode"
+    assert line["metric"] == "ODE theta-likelihoods/s" and line["higher_is_better"] is True
+    assert line["config"] == bench.ode_config(bench.ode_workload(64))
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
