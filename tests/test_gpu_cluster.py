@@ -57,10 +57,13 @@ def check(pf, w_net, th, x0, times, y, C, sigma, N, seed, cb, model=None, budget
     return g
 
 
-@pytest.mark.parametrize("cb,N", [(2, 1000), (3, 1000), (4, 257), (8, 1000), (8, 37), (5, 6)])
+@pytest.mark.parametrize("cb,N", [(2, 1000), (3, 1000), (4, 257), (8, 1000), (8, 37), (5, 6),
+                                  (8, 16384)])
 def test_gene_expression_split(pf, cb, N):
     """Even and ragged shares (N = 37 over 8 blocks: 5 particles each, 2 in
-    the last block; N = 6 over 5 blocks: 2, 2, 2, 0 -> rejected, see below)."""
+    the last block; N = 6 over 5 blocks: 2, 2, 2, 0 -> rejected, see below),
+    and the maximum population (16384 particles, 2048 per block; the one-block
+    filter it is compared with runs from the global-memory slab)."""
     w = W.gene_expression().subset(T=2, K=8)
     if N - (cb - 1) * -(-N // cb) < 1:
         with pytest.raises(pf.PfError) as e:
