@@ -24,11 +24,14 @@
  *   - A numerical failure of one theta does not fail the call: it is reported
  *     in status[m] and loglik[m] is -inf (PF_ST_BUDGET, PF_ST_NONFINITE) or
  *     NaN (PF_ST_INVALID_THETA).
- *   - Each result depends only on (problem, theta row, its row index m within
- *     the call, N, seed, event budget), never on the other rows of the batch.
+ *   - Each result depends only on (problem, theta row, its theta id, N,
+ *     seed, event budget), never on the other rows of the batch.  The theta
+ *     id of row m is m unless the caller gives ids (pf_options.theta_ids,
+ *     pf_request.theta_id_base), so that a batch split over several calls,
+ *     requests or processes reproduces the values of the whole batch.
  *   - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key = seed and
- *     counter = (draw j, particle i, (trajectory << 20) | interval k, row m);
- *     hence K < 2^20 and T < 2^12.
+ *     counter = (draw j, particle i, (trajectory << 20) | interval k, theta
+ *     id); hence K < 2^20 and T < 2^12.
  *   - No function keeps a caller pointer after it returns.
  */
 #ifndef PF1606_H
@@ -145,6 +148,11 @@ typedef struct {
  *                 idle).  Every block must hold at least one particle
  *                 (N > (C - 1) ceil(N / C)) and its share must fit in shared
  *                 memory; otherwise PF_EINVAL.
+ *   theta_ids     optional [M] uint32 (same memory space as thetas): the
+ *                 theta id of row m in the random-number counter (NULL: m).
+ *                 Rows with equal (theta row, theta id) get equal results
+ *                 wherever they sit, so rows a..b of a batch evaluated alone
+ *                 with theta_ids = a..b reproduce the whole batch's rows.
  *   Diagnostics are defined only for filters whose status is PF_ST_OK.
  */
 /*
@@ -203,6 +211,7 @@ typedef struct {
     double reject_below;
     const pf_model *model;
     int32_t cluster_blocks;
+    const uint32_t *theta_ids;
 } pf_options;
 
 /*
@@ -321,10 +330,19 @@ int pf_erk_loglik(const double *thetas, int64_t M, const double *switch_times,
  * reserved the GPU), a latency-critical serving loop that cannot afford the
  * allocator's synchronisation and unpredictable cost on its request path, or
  * a plug-in that must not grow the host application's device footprint after
- * it is loaded.  This entry point computes exactly what pf_loglik computes
- * and allocates nothing: its per-filter scratch (and the copy of obs_times)
- * lives in one static device array of PF_NOALLOC_SCRATCH_BYTES that every GPU
- * loading the library holds until the process exits.
+ * it is loaded.  This entry point allocates nothing: its per-filter scratch
+ * (and the copy of obs_times) lives in one static device array of
+ * PF_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  For the problems it accepts, its results equal
+ * pf_loglik's with default options (one block per filter, the basic model,
+ * theta ids 0..M-1).
+ *   Limits against pf_loglik: it takes no pf_options (no diagnostics, model
+ *   extensions, early rejection, cluster split, launch order or theta ids),
+ *   and it runs only populations that fit in shared memory: N (12 + 4U) bytes
+ *   plus the block's tables within the device's per-block opt-in limit (about
+ *   9 800 particles of 2 species, 3 700 of 10).  Larger populations, which
+ *   pf_loglik runs from global-memory slabs that it allocates, are refused
+ *   with PF_EINVAL before any device work.
  *   thetas [M][d], y [T][K][P], loglik [M] and status [M] (status may be NULL)
  *   are DEVICE pointers on the current device; the network, x0, obs_times, C
  *   and sigma are host arrays.  Work is enqueued on `stream` (NULL = legacy
@@ -334,10 +352,15 @@ int pf_erk_loglik(const double *thetas, int64_t M, const double *switch_times,
  *   PF_EINVAL before any device work.  event_budget 0 = default.
  *   The first call on a device looks the array's device address up
  *   (cudaGetSymbolAddress) and caches it; make that first call before any
- *   stream capture.  All calls share the one array and nothing in it needs
- *   to start at zero (every scratch entry is written before it is read), but
- *   calls whose work overlaps on the GPU (different streams, or host threads)
- *   race on it: serialise them.
+ *   stream capture.  Every call copies obs_times from the host into the
+ *   scratch with cudaMemcpyAsync on `stream`: from pageable memory the copy
+ *   is staged before the call returns; from pinned memory it runs when the
+ *   stream reaches it, so obs_times must then stay valid and unchanged until
+ *   then.  Calls are not meant to be captured into a CUDA graph.  All calls
+ *   share the one array and nothing in it needs to start at zero (every
+ *   scratch entry is written before it is read), but calls whose work
+ *   overlaps on the GPU (different streams, or host threads) race on it:
+ *   serialise them.
  * Returns PF_OK or a negative code, like pf_loglik.
  */
 #define PF_NOALLOC_SCRATCH_BYTES (16u << 20)
@@ -399,7 +422,10 @@ int pf_ctx_load_problem_model(pf_ctx *ctx, const pf_network *net, int32_t d, con
  * observation times to use (0 = all of the problem's).  event_budget 0 =
  * default.  loglik_threshold: the level-set threshold log epsilon_k of
  * Alg. 2; when finite, rows certainly below it stop early with
- * PF_ST_REJECTED (as pf_options.early_reject); NaN = evaluate every row fully. */
+ * PF_ST_REJECTED (as pf_options.early_reject); NaN = evaluate every row fully.
+ * theta_id_base: row m's theta id in the random-number counter is
+ * theta_id_base + m (< 2^32), so that a level set's batch split over several
+ * requests gives the values of one request over the whole batch. */
 typedef struct {
     int32_t problem_id;
     int32_t d;
@@ -412,6 +438,7 @@ typedef struct {
     double loglik_threshold;
     double *loglik;        /* [M] out */
     uint8_t *status;       /* [M] out, may be NULL */
+    uint32_t theta_id_base;
 } pf_request;
 
 /*
@@ -486,12 +513,14 @@ int pf_fp64_probe(int32_t kind, int32_t blocks, int32_t threads, int64_t iters,
                   double *elapsed_ms, double *checksum);
 
 /*
- * pf_neg_log_u53 -- the device logarithm the SSA kernel uses for the waiting
- * time tau = -log(u1) / a0 (Sec. "The stochastic birth-death Model": SSA),
- * exposed for accuracy tests: out[i] = -log(v[i] * 2^-53) for
- * 1 <= v[i] <= 2^53 (u1 in (0, 1]).  Table-driven (Tang, ACM TOMS 16(4),
- * 1990), 11 FP64 operations.  Host pointers; synchronous.  Returns PF_OK,
- * PF_EINVAL (a v[i] out of range), PF_ENOMEM or PF_ECUDA.
+ * pf_neg_log_u53 -- the device logarithm of the SSA kernel's exponential
+ * variates, exposed for accuracy tests: out[i] = -log(v[i] * 2^-53) for
+ * 1 <= v[i] <= 2^53 (u in (0, 1]).  The kernels draw the waiting time's
+ * Exp(1) variate by a ziggurat (pf_exp_variates) and call this logarithm
+ * only in the ziggurat's tail, r - log(u), about 4e-5 of the draws (and in
+ * the scheduling pilot's waiting times).  Table-driven (Tang, ACM TOMS
+ * 16(4), 1990), 12 FP64 operations.  Host pointers; synchronous.  Returns
+ * PF_OK, PF_EINVAL (a v[i] out of range), PF_ENOMEM or PF_ECUDA.
  */
 int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n);
 
@@ -500,7 +529,7 @@ int pf_neg_log_u53(const uint64_t *v, double *out, int64_t n);
  * (tau = E / a0; Gillespie's direct method, Sec. "The stochastic birth-death
  * Model"), exposed for tests: out[k] = the variate of draw counter k of
  * particle 0, interval word 0, theta row 0 under key `seed`.  Ziggurat method
- * (Marsaglia & Tsang, J. Stat. Softw. 5(8), 2000), 256 layers.  Host output;
+ * (Marsaglia & Tsang, J. Stat. Softw. 5(8), 2000), 2048 layers.  Host output;
  * synchronous.  Returns PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.
  */
 int pf_exp_variates(uint64_t seed, int64_t n, double *out);

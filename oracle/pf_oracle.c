@@ -21,7 +21,7 @@
  *   - the product over trajectories p(y|theta) = prod_m p(y^m|theta), Supp. I,
  *     taken as a sum of logarithms.
  *
- * Readings where the paper is silent (each is listed in the design doc):
+ * Readings where the paper is silent:
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter = (draw j, particle i, (trajectory << 20) | interval k, theta m);
  *     the resampling uniform of interval k uses particle lane 0xFFFFFFFF;
@@ -500,13 +500,16 @@ static int check_model(const orc_model *mdl, const int32_t *x0, int U, int P) {
 /*
  * Log-likelihood of M theta rows.  theta_ids[M] (or NULL = 0..M-1) gives the
  * global theta index used in the random-number counter, so that a subset of a
- * larger batch reproduces that batch's values.
+ * larger batch reproduces that batch's values; traj_ids[T] (or NULL = 0..T-1)
+ * likewise gives each trajectory's index in the counter, so that one
+ * trajectory of a problem can be evaluated alone.
  * Per-(theta, trajectory) outputs ll_traj, events, digest are [M][T]
  * (each may be NULL); final_states is [M][T][N][U] (may be NULL).
  */
 int orc_pf_loglik(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod,
                   const int32_t *rate_index, const double *rate_coef, const double *thetas,
-                  int64_t M, int32_t d, const int64_t *theta_ids, const int32_t *x0,
+                  int64_t M, int32_t d, const int64_t *theta_ids, const int64_t *traj_ids,
+                  const int32_t *x0,
                   const int32_t *x0_hi, const double *obs_times, int32_t K, const double *y,
                   int32_t T, int32_t P, const double *Cm, const double *sigma,
                   const double *obs_offset, const double *obs_var, int32_t N, uint64_t seed,
@@ -518,6 +521,9 @@ int orc_pf_loglik(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
     zig_init();
     if (N < 1 || N > 16384 || K < 1 || T < 1 || P < 1 || T >= 4096 || K >= (1 << 20))
         return ORC_EINVAL;
+    if (traj_ids)
+        for (int traj = 0; traj < T; traj++)
+            if (traj_ids[traj] < 0 || traj_ids[traj] >= 4096) return ORC_EINVAL;
     for (int64_t mi = 0; mi < M; mi++) {
         const double *theta = &thetas[mi * d];
         uint32_t m = (uint32_t)(theta_ids ? theta_ids[mi] : mi);
@@ -526,8 +532,9 @@ int orc_pf_loglik(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
         for (int traj = 0; traj < T; traj++) {
             filter_result fr;
             int32_t *fs = final_states ? &final_states[((size_t)mi * T + traj) * (size_t)N * U] : NULL;
+            uint32_t tid = (uint32_t)(traj_ids ? traj_ids[traj] : traj);
             int rc = run_filter(&net, &mdl, theta, x0, obs_times, K, &y[(size_t)traj * K * P], P,
-                                Cm, sigma, N, seed, budget, (uint32_t)traj, m, &fr, fs);
+                                Cm, sigma, N, seed, budget, tid, m, &fr, fs);
             if (rc) return rc;
             if (ll_traj) ll_traj[mi * T + traj] = fr.ll;
             if (events) events[mi * T + traj] = fr.events;

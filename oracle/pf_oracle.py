@@ -42,8 +42,8 @@ def _bind(path: Path) -> ct.CDLL:
     lib.orc_resample_systematic.argtypes = [P, ct.c_int32, ct.c_uint64, P]
     lib.orc_resample_systematic.restype = None
     lib.orc_pf_loglik.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, P, ct.c_int64, ct.c_int32,
-                                  P, P, P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P, P, P,
-                                  ct.c_int32, ct.c_uint64, ct.c_uint64, P, P, P, P, P, P]
+                                  P, P, P, P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P, P,
+                                  P, ct.c_int32, ct.c_uint64, ct.c_uint64, P, P, P, P, P, P]
     lib.orc_pf_loglik.restype = ct.c_int
     lib.orc_ssa_paths.argtypes = [ct.c_int32, ct.c_int32, P, P, P, P, P, ct.c_int32, P, P,
                                   ct.c_int32, ct.c_int64, ct.c_uint64, ct.c_uint64, P, P, P]
@@ -119,8 +119,13 @@ class Oracle:
 
     def pf_loglik(self, net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, seed: int,
                       budget: int = DEFAULT_BUDGET, theta_ids=None,
-                      want_final_states: bool = False, model: dict | None = None):
+                      want_final_states: bool = False, model: dict | None = None,
+                      traj_ids=None):
         """Filter log-likelihood of every theta row.
+
+        theta_ids [M] / traj_ids [T] (optional): the rows' and trajectories'
+        indices in the random-number counter (default 0..M-1 and 0..T-1), so
+        that part of a larger problem reproduces the whole problem's values.
 
         net: {"reactants": [R][U], "products": [R][U], "rate_index": [R] or None}
         y: [T][K][P].  model (optional): {"rate_coef": [R][d], "x0_hi": [U],
@@ -139,6 +144,7 @@ class Oracle:
             th = th[None, :]
         M, d = th.shape
         ids = None if theta_ids is None else _c(theta_ids, np.int64)
+        tids = None if traj_ids is None else _c(traj_ids, np.int64)
         x0 = _c(x0, np.int32)
         ts = _c(obs_times, np.float64)
         yy = _c(y, np.float64)
@@ -163,8 +169,10 @@ class Oracle:
             "digest": np.zeros((M, T), np.uint64),
         }
         fs = np.zeros((M, T, N, U), np.int32) if want_final_states else None
+        if tids is not None and tids.shape != (T,):
+            raise ValueError("traj_ids must have one entry per trajectory")
         rc = lib.orc_pf_loglik(U, R, _ptr(reac), _ptr(prod), _ptr(ri), _ptr(rc_), _ptr(th), M, d,
-                               _ptr(ids), _ptr(x0), _ptr(xhi), _ptr(ts), K, _ptr(yy), T, P,
+                               _ptr(ids), _ptr(tids), _ptr(x0), _ptr(xhi), _ptr(ts), K, _ptr(yy), T, P,
                                _ptr(Cm), _ptr(sg), _ptr(off), _ptr(ov), N,
                                ct.c_uint64(int(seed)), ct.c_uint64(int(budget)),
                                _ptr(out["loglik"]), _ptr(out["status"]), _ptr(out["ll_traj"]),

@@ -334,6 +334,16 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
             a.row_order = (const uint32_t *)b_order.p;
         }
     }
+    DevBuf b_ids;
+    if (o.theta_ids) {
+        if (o.device_ptrs) {
+            a.theta_ids = o.theta_ids;
+        } else {
+            PF_CUDA(b_ids.alloc(sizeof(uint32_t) * M, s), "alloc theta ids");
+            PF_CUDA(cudaMemcpyAsync(b_ids.p, o.theta_ids, sizeof(uint32_t) * M, cudaMemcpyHostToDevice, s), "copy theta ids");
+            a.theta_ids = (const uint32_t *)b_ids.p;
+        }
+    }
     if (o.schedule < 0 || o.schedule > PF_SCHED_HEAVY_FIRST) return fail(PF_EINVAL, "unknown schedule %d", o.schedule);
     if (heavy_first) {
         PF_CUDA(b_cost.alloc(sizeof(uint32_t) * M, s), "alloc schedule");

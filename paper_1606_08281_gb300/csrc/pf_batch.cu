@@ -60,6 +60,7 @@ struct RequestDev {
     int64_t row_base;         // first row of the slot's output arena
     uint64_t seed, budget;
     int32_t d, N, K, T;
+    uint32_t id_base;         // theta id of row 0 in the random-number counter
     double *acc;              // this request's rejection bounds (row_base-relative), or null
     double reject_below;
     double slack;
@@ -135,7 +136,7 @@ batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *ite
         job.y = rq.prob->y + static_cast<int64_t>(traj) * rq.prob->K * sh.net.P;
         job.K = rq.K;
         job.N = rq.N;
-        job.mrow = row;
+        job.mrow = rq.id_base + row;
         job.traj = traj;
         job.seed = rq.seed;
         job.budget = rq.budget;
@@ -407,6 +408,8 @@ int check_request(pf_ctx *ctx, const pf_request &r, ReqState &st) {
     if (r.M < 0 || (r.M > 0 && (!r.thetas || !r.loglik))) return fail(PF_EINVAL, "bad theta/output arrays");
     if (r.n_particles < 1 || r.n_particles > ctx->max_particles)
         return fail(PF_EINVAL, "n_particles %d outside 1..%d", r.n_particles, ctx->max_particles);
+    if (static_cast<uint64_t>(r.theta_id_base) + static_cast<uint64_t>(std::max<int64_t>(r.M, 0)) > 0x100000000ull)
+        return fail(PF_EINVAL, "theta_id_base + M must be <= 2^32");
     const int K = r.K_use ? r.K_use : p.K;
     if (K < 1 || K > p.K) return fail(PF_EINVAL, "K_use %d outside 1..%d", r.K_use, p.K);
     const uint64_t budget = r.event_budget ? r.event_budget : PF_DEFAULT_EVENT_BUDGET;
@@ -457,6 +460,7 @@ int launch_batch(pf_ctx *ctx, int si, const std::vector<ReqState *> &batch) {
         rd.filter_base = filters;
         rd.row_base = rows;
         rd.seed = r.seed;
+        rd.id_base = r.theta_id_base;
         rd.budget = r.event_budget;
         rd.d = r.d;
         rd.N = r.n_particles;

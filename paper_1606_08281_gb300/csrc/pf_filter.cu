@@ -28,6 +28,8 @@
 #include <cmath>
 #include <cstdint>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "pf_device.cuh"
 
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__(128, 4) filter_kernel(const FilterArgs args) {
     job.y = args.y + static_cast<int64_t>(traj) * args.K * args.net.P;
     job.K = args.K;
     job.N = args.N;
-    job.mrow = static_cast<uint32_t>(mrow);
+    job.mrow = args.theta_ids ? args.theta_ids[mrow] : static_cast<uint32_t>(mrow);
     job.traj = traj;
     job.seed = args.seed;
     job.budget = args.budget;
@@ -105,7 +107,7 @@ __global__ void __launch_bounds__(128, 4) filter_kernel_cluster(const FilterArgs
     job.y = args.y + static_cast<int64_t>(traj) * args.K * args.net.P;
     job.K = args.K;
     job.N = args.N;
-    job.mrow = static_cast<uint32_t>(mrow);
+    job.mrow = args.theta_ids ? args.theta_ids[mrow] : static_cast<uint32_t>(mrow);
     job.traj = traj;
     job.seed = args.seed;
     job.budget = args.budget;
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(128, 4) filter_kernel_global(const FilterArgs 
         job.y = args.y + static_cast<int64_t>(traj) * args.K * args.net.P;
         job.K = args.K;
         job.N = args.N;
-        job.mrow = static_cast<uint32_t>(mrow);
+        job.mrow = args.theta_ids ? args.theta_ids[mrow] : static_cast<uint32_t>(mrow);
         job.traj = traj;
         job.seed = args.seed;
         job.budget = args.budget;
@@ -314,9 +316,8 @@ __global__ void philox_kernel(const uint32_t *ctr, const uint32_t *key, uint32_t
 
 template <int RM, int UM>
 int launch_tier(const FilterArgs &a, int B, size_t smem, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(filter_kernel<RM, UM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = static_cast<cudaError_t>(
+        raise_smem_limit(reinterpret_cast<const void *>(filter_kernel<RM, UM>)));
     if (e != cudaSuccess) return e;
     const int64_t F = a.M * a.T;
     filter_kernel<RM, UM><<<static_cast<unsigned>(F), B, smem, s>>>(a);
@@ -325,9 +326,8 @@ int launch_tier(const FilterArgs &a, int B, size_t smem, cudaStream_t s) {
 
 template <int RM, int UM>
 int launch_tier_cluster(const FilterArgs &a, int B, size_t smem, int C, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(filter_kernel_cluster<RM, UM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = static_cast<cudaError_t>(
+        raise_smem_limit(reinterpret_cast<const void *>(filter_kernel_cluster<RM, UM>)));
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(static_cast<unsigned>(a.M * a.T * C));
@@ -347,6 +347,33 @@ int launch_tier_cluster(const FilterArgs &a, int B, size_t smem, int C, cudaStre
 }
 
 }  // namespace
+
+// The dynamic shared-memory limit of a kernel is a process-wide attribute.
+// It is raised once per kernel and device to the largest size a launch of it
+// can use (the device's opt-in maximum less the kernel's static shared
+// memory) and never lowered, so concurrent callers with different
+// populations cannot change it under each other's launches.
+int raise_smem_limit(const void *kernel) {
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    for (const auto &kd : done)
+        if (kd.first == kernel && kd.second == dev) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - static_cast<int>(fa.sharedSizeBytes));
+    if (e != cudaSuccess) return e;
+    done.emplace_back(kernel, dev);
+    return cudaSuccess;
+}
 
 size_t cluster_smem_bytes(int N, int C, int U, bool digest) {
     return cluster_share_bytes(N, C, U, digest);

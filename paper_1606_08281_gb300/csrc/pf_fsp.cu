@@ -454,8 +454,8 @@ extern "C" int pf_fsp_loglik(const pf_network *net, const double *thetas, int64_
         smem = smem_coef;
         a.coef_smem = 1;
     }
-    FSP_CUDA(cudaFuncSetAttribute(pf::fsp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)smem), "fsp smem attribute");
+    FSP_CUDA(static_cast<cudaError_t>(pf::raise_smem_limit(reinterpret_cast<const void *>(pf::fsp_kernel))),
+             "fsp smem attribute");
     pf::fsp_kernel<<<(unsigned)F, threads, smem, s>>>(a);
     FSP_CUDA(cudaGetLastError(), "fsp launch");
     pf::fsp_reduce_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(a.ll_f, a.st_f, M, T, d_ll, d_st);

@@ -58,6 +58,7 @@ struct FilterArgs {
     uint64_t *dg_f;          // may be null: digest not computed
     int32_t *final_states;   // [M*T][N][U], may be null
     const uint32_t *row_order;  // [M] theta rows in launch order (null: 0..M-1)
+    const uint32_t *theta_ids;  // [M] theta id of each row in the random-number counter (null: m)
     double *acc;                // [M] running upper bounds for early rejection (null: off)
     double reject_below;
     double slack;               // upper bound of one per-time-point log increment, >= 0
@@ -82,6 +83,12 @@ int reaction_tier(int R);
 int launch_filter(const FilterArgs &a, int block_threads, double *loglik, uint8_t *status,
                   void *stream, unsigned char *slabs = nullptr, size_t slab_bytes = 0,
                   int grid = 0);
+
+// Raise a kernel's dynamic shared-memory limit (a process-wide attribute)
+// once per device to the largest size any launch of it can use; never lowers
+// it, so concurrent callers cannot undercut each other's launches.  Returns a
+// cudaError_t value.
+int raise_smem_limit(const void *kernel);
 
 // Resident blocks for the global-memory variant on a GPU with `sms` SMs.
 int global_grid(int sms);

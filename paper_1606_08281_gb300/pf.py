@@ -51,7 +51,7 @@ class pf_request(ct.Structure):
                 ("M", ct.c_int64), ("n_particles", ct.c_int32), ("K_use", ct.c_int32),
                 ("seed", ct.c_uint64), ("event_budget", ct.c_uint64),
                 ("loglik_threshold", ct.c_double), ("loglik", ct.c_void_p),
-                ("status", ct.c_void_p)]
+                ("status", ct.c_void_p), ("theta_id_base", ct.c_uint32)]
 
 
 class pf_model(ct.Structure):
@@ -66,7 +66,7 @@ class pf_options(ct.Structure):
                 ("final_states", ct.c_void_p), ("schedule", ct.c_int32),
                 ("early_reject", ct.c_int32), ("row_order", ct.c_void_p),
                 ("reject_below", ct.c_double), ("model", ct.POINTER(pf_model)),
-                ("cluster_blocks", ct.c_int32)]
+                ("cluster_blocks", ct.c_int32), ("theta_ids", ct.c_void_p)]
 
 
 class pf_fsp_options(ct.Structure):
@@ -219,13 +219,16 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
               event_budget: int = 0, block_threads: int = 0, stream=None,
               diagnostics: bool = False, final_states: bool = False, out=None,
               schedule: int = PF_SCHED_AUTO, row_order=None, reject_below=None,
-              model: dict | None = None, cluster_blocks: int = 0):
+              model: dict | None = None, cluster_blocks: int = 0, theta_ids=None):
     """Log-likelihood of every theta row (see pf_loglik in include/pf1606.h).
 
     model: optional Lac-Gfp extensions {"rate_coef", "x0_hi", "obs_offset",
     "obs_var"} (pf_model; host arrays).
     cluster_blocks: 2..8 splits each filter over a thread-block cluster of
     that many blocks (pf_options.cluster_blocks); 0 = one block per filter.
+    theta_ids: optional [M] uint32 theta ids of the rows in the random-number
+    counter (pf_options.theta_ids; default 0..M-1), in the memory space of
+    `thetas` (a uint32-valued CUDA tensor of dtype int32 in device mode).
 
     Returns a dict with 'loglik' [M] and 'status' [M]; with diagnostics=True
     also 'll_traj', 'events', 'digest' [M][T]; with final_states=True also
@@ -288,12 +291,26 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
     else:
         ro = _host(row_order, np.uint32)
         p_ro = _hptr(ro)
+    if theta_ids is None:
+        p_ids = None
+    elif device:
+        ids = theta_ids.contiguous()
+        ok_types = (torch.int32, getattr(torch, "uint32", torch.int32))
+        if ids.dtype not in ok_types or ids.numel() != M or not ids.is_cuda:
+            raise ValueError("theta_ids must be a CUDA tensor of M 32-bit ids")
+        p_ids = ids.data_ptr()
+    else:
+        ids = np.asarray(theta_ids)
+        if ids.shape != (M,) or ids.min(initial=0) < 0 or ids.max(initial=0) >= 2**32:
+            raise ValueError("theta_ids must hold M ids in 0..2^32-1")
+        ids = _host(ids, np.uint32)
+        p_ids = _hptr(ids)
     mdl = _Model(model)
     opt = pf_options(int(event_budget), 1 if device else 0, int(block_threads),
                      stream if device else None, ptr("ll_traj"), ptr("events"), ptr("digest"),
                      ptr("final_states"), int(schedule), 0 if reject_below is None else 1, p_ro,
                      float("nan") if reject_below is None else float(reject_below), mdl.ptr(),
-                     int(cluster_blocks))
+                     int(cluster_blocks), p_ids)
     rc = lib.pf_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), p_ts, K, p_y, T, P, _hptr(Ch),
                        _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
                        ptr("loglik"), ptr("status"), ct.byref(opt))
@@ -460,19 +477,45 @@ def pf_loglik_noalloc(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles
                       seed: int, loglik, status=None, *, event_budget: int = 0, stream=None):
     """Allocation-free pf_loglik (see include/pf1606.h).  thetas [M][d], y
     [T][K][P], loglik [M] and status [M] are torch CUDA tensors the caller owns;
-    the call enqueues on `stream` (default: the current torch stream)."""
+    the call enqueues on `stream` (default: the current torch stream).
+
+    The tensors are checked, never copied: a temporary copy could be freed
+    before the kernel that reads it runs.  Each must be a contiguous CUDA
+    tensor on the current device with the right dtype (float64; status
+    uint8) and enough elements, else ValueError."""
     import torch
     lib = load()
     n = _Net(net)
     U = n.s.n_species
     th = thetas
+    if getattr(th, "ndim", 0) != 2 or getattr(y, "ndim", 0) != 3:
+        raise ValueError("thetas must be [M][d] and y [T][K][P]")
     M, d = th.shape
     T, K, P = y.shape
+    dev = torch.cuda.current_device()
+
+    def need(name, t, dtype, numel):
+        if not (type(t).__module__.startswith("torch") and t.is_cuda):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+        if t.dtype != dtype:
+            raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() < numel:
+            raise ValueError(f"{name} has {t.numel()} elements, needs {numel}")
+
+    need("thetas", th, torch.float64, M * d)
+    need("y", y, torch.float64, T * K * P)
+    need("loglik", loglik, torch.float64, M)
+    if status is not None:
+        need("status", status, torch.uint8, M)
     ts = _host(obs_times, np.float64)
     Ch = _host(C, np.float64).reshape(P, U)
     sg = _host(sigma, np.float64).reshape(P)
     if stream is None:
-        stream = torch.cuda.current_stream(th.device).cuda_stream
+        stream = torch.cuda.current_stream(dev).cuda_stream
     rc = lib.pf_loglik_noalloc(ct.byref(n.s), th.data_ptr(), M, d, _hptr(_host(x0, np.int32)),
                                _hptr(ts), K, y.data_ptr(), T, P, _hptr(Ch), _hptr(sg),
                                int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
@@ -535,7 +578,8 @@ class Request:
     """Host arrays of one request, kept alive until pf_poll reports completion."""
 
     def __init__(self, problem_id: int, thetas, n_particles: int, seed: int, K_use: int = 0,
-                 event_budget: int = 0, loglik_threshold: float = float("nan")):
+                 event_budget: int = 0, loglik_threshold: float = float("nan"),
+                 theta_id_base: int = 0):
         self.thetas = _host(thetas, np.float64)
         if self.thetas.ndim == 1:
             self.thetas = self.thetas[None, :]
@@ -545,7 +589,7 @@ class Request:
         self.s = pf_request(int(problem_id), int(d), _hptr(self.thetas), int(M),
                             int(n_particles), int(K_use), int(seed) & (2**64 - 1),
                             int(event_budget), float(loglik_threshold),
-                            _hptr(self.loglik), _hptr(self.status))
+                            _hptr(self.loglik), _hptr(self.status), int(theta_id_base))
         self.id = None
         self.t_submit = self.t_done = None
 

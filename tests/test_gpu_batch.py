@@ -183,3 +183,60 @@ def test_batch_covers_every_tier(pf):
             assert np.array_equal(r.loglik, ref["loglik"]), (N, r.loglik, ref["loglik"])
     finally:
         pf.pf_ctx_destroy(c)
+
+
+def oracle_rows(w, th, N, seed, K, ids=None):
+    from oracle import pf_oracle
+    return pf_oracle.pf_loglik(w.net, th, w.x0, w.obs_times[:K], w.observations()[:, :K, :], w.C,
+                               w.sigma, N, seed, theta_ids=ids)
+
+
+def test_batch_matches_the_oracle(pf, ctx, problems):
+    """The context's results against the oracle directly (not only against
+    pf_loglik): every network, on-chip and global-slab populations, requests
+    with theta id bases."""
+    specs = [("birth_death", 25, 100, 20, 61, 0), ("gene_expression", 6, 1000, 10, 62, 500),
+             ("gene_expression", 2, 2048, 5, 63, 0), ("cascade", 2, 256, 4, 64, 9000)]
+    reqs = []
+    for name, M, N, K, seed, base in specs:
+        pid, w = problems[name]
+        th = W.log_uniform(np.random.default_rng(seed), w.prior_lo, w.prior_hi, M)
+        reqs.append((pf.Request(pid, th, N, seed, K_use=K, theta_id_base=base), w, th, N, seed, K,
+                     base))
+    pf.pf_ctx_run_batch(ctx, [r[0] for r in reqs])
+    for r, w, th, N, seed, K, base in reqs:
+        o = oracle_rows(w, th, N, seed, K, ids=np.arange(base, base + len(th)))
+        assert (r.status == o["status"]).all(), w.name
+        np.testing.assert_allclose(r.loglik, o["loglik"], rtol=1e-9, atol=0)
+
+
+def rejection_threshold(values: np.ndarray) -> float:
+    """A threshold between two neighbouring values near the median, so that no
+    value lies within rounding of it (the decision is then exact)."""
+    v = np.sort(values[np.isfinite(values)])
+    i = len(v) // 2
+    gaps = np.diff(v[max(0, i - 5): i + 6])
+    j = max(0, i - 5) + int(np.argmax(gaps))
+    return float(0.5 * (v[j] + v[j + 1]))
+
+
+def test_early_rejection_decisions_against_the_oracle(pf, ctx, problems):
+    """REJECTED exactly for the rows whose full oracle log-likelihood is below
+    the threshold (Alg. 2 keeps theta only if l_hat >= epsilon); every other
+    row equals the oracle's value.  Plain call and batch request."""
+    pid, w = problems["gene_expression"]
+    th = W.log_uniform(np.random.default_rng(91), w.prior_lo, w.prior_hi, 48)
+    N, seed, K = 200, 19, 12
+    o = oracle_rows(w, th, N, seed, K)
+    thr = rejection_threshold(o["loglik"])
+    below = o["loglik"] < thr
+    assert 10 < below.sum() < 38
+    plain_cut = pf.pf_loglik(w.net, th, w.x0, w.obs_times[:K], w.observations()[:, :K, :], w.C,
+                             w.sigma, N, seed, reject_below=thr)
+    req = pf.Request(pid, th, N, seed, K_use=K, loglik_threshold=thr)
+    pf.pf_ctx_run_batch(ctx, [req])
+    for st, ll in ((plain_cut["status"], plain_cut["loglik"]), (req.status, req.loglik)):
+        assert (st[below] == pf.PF_ST_REJECTED).all()
+        assert (st[~below] == 0).all()
+        np.testing.assert_allclose(ll[~below], o["loglik"][~below], rtol=1e-9, atol=0)
+        assert np.isneginf(ll[below]).all()

@@ -75,3 +75,49 @@ def test_noalloc_rejects_problems_beyond_its_scratch(pf):
         None)
     assert rc == pf.PF_EINVAL
     assert "scratch" in pf.pf_last_error()
+
+
+def test_noalloc_refuses_populations_beyond_shared_memory(pf):
+    """pf_loglik runs populations beyond shared memory from global slabs it
+    allocates; the allocation-free entry point refuses them (PF_EINVAL) on
+    the host, before any device work."""
+    import ctypes as ct
+
+    import torch
+    w = W.gene_expression().subset(T=1, K=3)
+    dev = torch.device("cuda:0")
+    th = torch.from_numpy(w.thetas(2)).to(dev)
+    y = torch.from_numpy(w.observations()).to(dev)
+    ll = torch.empty(2, dtype=torch.float64, device=dev)
+    n = pf._Net(w.net)
+    ts = np.ascontiguousarray(w.obs_times)
+    rc = pf.load().pf_loglik_noalloc(
+        ct.byref(n.s), th.data_ptr(), 2, 4, pf._hptr(np.zeros(2, np.int32)), pf._hptr(ts), 3,
+        y.data_ptr(), 1, 1, pf._hptr(np.ascontiguousarray(w.C)), pf._hptr(w.sigma), 16384,
+        ct.c_uint64(1), ll.data_ptr(), None, ct.c_uint64(0), None)
+    assert rc == pf.PF_EINVAL
+    assert "shared memory" in pf.pf_last_error()
+
+
+def test_noalloc_wrapper_checks_its_tensors(pf):
+    """The binding refuses, without copying, tensors the call cannot read as
+    they are: a wrong dtype, a non-contiguous view, a host tensor, a short
+    output."""
+    import torch
+    w = W.birth_death()
+    dev = torch.device("cuda:0")
+    th = torch.from_numpy(w.thetas(8)).to(dev)
+    y = torch.from_numpy(w.observations()).to(dev)
+    ll = torch.empty(8, dtype=torch.float64, device=dev)
+    args = (w.net, th, w.x0, w.obs_times, y, w.C, w.sigma, 64, 5)
+    with pytest.raises(ValueError, match="float64"):
+        pf.pf_loglik_noalloc(w.net, th.float(), w.x0, w.obs_times, y, w.C, w.sigma, 64, 5, ll)
+    wide = torch.from_numpy(np.repeat(w.thetas(8), 2, axis=1)).to(dev)
+    with pytest.raises(ValueError, match="contiguous"):
+        pf.pf_loglik_noalloc(w.net, wide[:, ::2], w.x0, w.obs_times, y, w.C, w.sigma, 64, 5, ll)
+    with pytest.raises(ValueError, match="CUDA"):
+        pf.pf_loglik_noalloc(*args, ll.cpu())
+    with pytest.raises(ValueError, match="elements"):
+        pf.pf_loglik_noalloc(*args, ll[:4])
+    with pytest.raises(ValueError, match="uint8"):
+        pf.pf_loglik_noalloc(*args, ll, torch.empty(8, dtype=torch.int32, device=dev))
