@@ -338,11 +338,38 @@ typedef struct {
 /* Log-weight rounded to a multiple of 2^-20 (exact scaling, ties to even). */
 static double grid20(double e) { return ldexp(nearbyint(ldexp(e, 20)), -20); }
 
+/* Integer resampling weights q_i = floor(2^32 exp(e_i - emax)); with a
+ * state-dependent variance (svar) from the log-weights rounded by grid20. */
+static void quantise_weights(const double *e, int N, double emax, int svar, uint64_t *q) {
+    for (int i = 0; i < N; i++) {
+        if (svar)
+            q[i] = (uint64_t)ldexp(exp(grid20(e[i]) - grid20(emax)), 32);
+        else
+            q[i] = (uint64_t)ldexp(exp(e[i] - emax), 32);
+    }
+}
+
+/* Optional record of one interval k of a filter, for tracing a divergence:
+ * the states entering its simulation (after resampling), the ancestors, the
+ * log-weights and integer weights of interval k-1 that chose them (zero at
+ * k = 0), the states after its simulation and the reactions each particle
+ * fired in it.  Filled by copying; the filter's arithmetic is unchanged. */
+typedef struct {
+    int32_t k;
+    int64_t *x_start;   /* [N][U] */
+    int64_t *x_end;     /* [N][U] */
+    int32_t *anc;       /* [N] */
+    double *e_prev;     /* [N] */
+    uint64_t *q_prev;   /* [N] */
+    uint64_t *fired;    /* [N] */
+} orc_trace;
+
 static int run_filter(const orc_net *net, const orc_model *mdl, const double *theta,
                       const int32_t *x0, const double *obs_times, int K,
                       const double *y_traj /* [K][P] */, int P, const double *Cm,
                       const double *sigma, int N, uint64_t seed, uint64_t budget, uint32_t traj,
-                      uint32_t m, filter_result *res, int32_t *final_states /* [N][U] or NULL */) {
+                      uint32_t m, filter_result *res, int32_t *final_states /* [N][U] or NULL */,
+                      orc_trace *tr /* or NULL */) {
     int U = net->U, R = net->R;
     int64_t *x = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * U);
     int64_t *xn = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * U);
@@ -384,12 +411,7 @@ static int run_filter(const orc_net *net, const orc_model *mdl, const double *th
         uint32_t lane = (traj << 20) | (uint32_t)k;
         /* resample by the weights of observation k-1 (Supp. I, "Sample H indices") */
         if (k >= 1) {
-            for (int i = 0; i < N; i++) {
-                if (mdl->obs_var)
-                    q[i] = (uint64_t)ldexp(exp(grid20(e[i]) - grid20(emax)), 32);
-                else
-                    q[i] = (uint64_t)ldexp(exp(e[i] - emax), 32);
-            }
+            quantise_weights(e, N, emax, mdl->obs_var != NULL, q);
             uint32_t w[4];
             draw4(seed, 0u, 0xFFFFFFFFu, lane, m, w);
             uint64_t r64 = ((uint64_t)w[1] << 32) | w[0];
@@ -400,11 +422,24 @@ static int run_filter(const orc_net *net, const orc_model *mdl, const double *th
         } else {
             for (int j = 0; j < N; j++) anc[j] = j;
         }
+        int tracing = tr && tr->k == k;
+        if (tracing)
+            for (int j = 0; j < N; j++) {
+                tr->anc[j] = anc[j];
+                tr->e_prev[j] = k >= 1 ? e[j] : 0.0;
+                tr->q_prev[j] = k >= 1 ? q[j] : 0u;
+                for (int u = 0; u < U; u++) tr->x_start[(size_t)j * U + u] = x[(size_t)j * U + u];
+            }
         /* simulate every particle to the observation time (Supp. I, "Simulate X_t") */
         double t_k = obs_times[k];
-        for (int i = 0; i < N && status == ORC_OK; i++)
+        for (int i = 0; i < N && status == ORC_OK; i++) {
+            uint64_t before = events;
             status = ssa_advance(net, rate, &x[(size_t)i * U], t_prev, t_k, seed, (uint32_t)i,
                                  lane, m, budget, a, S, &events);
+            if (tracing) tr->fired[i] = events - before;
+        }
+        if (tracing)
+            for (int j = 0; j < N * U; j++) tr->x_end[j] = x[j];
         if (status != ORC_OK) break;
         for (int j = 0; j < N; j++)
             digest += slot_digest((uint32_t)k, (uint32_t)j, (uint32_t)anc[j], &x[(size_t)j * U], U);
@@ -534,7 +569,7 @@ int orc_pf_loglik(int32_t U, int32_t R, const int32_t *reac, const int32_t *prod
             int32_t *fs = final_states ? &final_states[((size_t)mi * T + traj) * (size_t)N * U] : NULL;
             uint32_t tid = (uint32_t)(traj_ids ? traj_ids[traj] : traj);
             int rc = run_filter(&net, &mdl, theta, x0, obs_times, K, &y[(size_t)traj * K * P], P,
-                                Cm, sigma, N, seed, budget, tid, m, &fr, fs);
+                                Cm, sigma, N, seed, budget, tid, m, &fr, fs, NULL);
             if (rc) return rc;
             if (ll_traj) ll_traj[mi * T + traj] = fr.ll;
             if (events) events[mi * T + traj] = fr.events;

@@ -43,6 +43,13 @@ MUTANTS = {
     "composed_rate_transposed": ("v = v + net->rate_coef[r * net->d + c] * theta[c];",
                                  "v = v + net->rate_coef[c * net->R + r] * theta[c];",
                                  "model_unbiased"),
+    "grid20_truncates": ("ldexp(nearbyint(ldexp(e, 20)), -20)", "ldexp(trunc(ldexp(e, 20)), -20)",
+                         "grid20"),
+    "grid20_width": ("ldexp(nearbyint(ldexp(e, 20)), -20)", "ldexp(nearbyint(ldexp(e, 19)), -19)",
+                     "grid20"),
+    "grid20_max_not_rounded": ("exp(grid20(e[i]) - grid20(emax))", "exp(grid20(e[i]) - emax)",
+                               "quantise"),
+    "grid20_dropped": ("exp(grid20(e[i]) - grid20(emax))", "exp(e[i] - emax)", "quantise"),
 }
 
 CHECKS = {
@@ -57,6 +64,8 @@ CHECKS = {
     "exp_law": lambda o, kat: pins.check_exp_variates(o),
     "init_uniform": lambda o, kat: pins.check_initial_uniform(o),
     "model_unbiased": lambda o, kat: pins.check_model_unbiased(o, S=150, N=100),
+    "grid20": lambda o, kat: pins.check_grid20(o),
+    "quantise": lambda o, kat: pins.check_quantised_weights(o),
 }
 
 

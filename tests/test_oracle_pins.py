@@ -456,3 +456,59 @@ def test_invalid_networks_rejected():
     with pytest.raises(ValueError):        # rate index out of range
         orc().pf_loglik({"reactants": [[1]], "products": [[0]], "rate_index": [2]}, [[1.0]],
                         [5], [1.0], np.zeros((1, 1, 1)), [[1.0]], [1.0], 4, 1)
+
+
+# --------------------------------------------------------------------------
+# log-weight rounding and integer weights of the resampling step
+# --------------------------------------------------------------------------
+def nearest_multiple_2m20(e: float) -> float:
+    """The multiple of 2^-20 nearest to e, ties to the even multiple, in
+    exact rational arithmetic (Python's round() of a Fraction is
+    round-half-even)."""
+    from fractions import Fraction
+    return float(Fraction(round(Fraction(e) * 2**20), 2**20))
+
+
+def check_grid20(o):
+    u = 2.0 ** -20
+    cases = {0.0: 0.0, 3 * u: 3 * u, -7 * u: -7 * u,            # already on the grid
+             0.5 * u: 0.0, 1.5 * u: 2 * u, 2.5 * u: 2 * u,    # ties go to the even multiple
+             -0.5 * u: 0.0, -1.5 * u: -2 * u, -2.5 * u: -2 * u,
+             0.3 * u: 0.0, 0.7 * u: u, -0.7 * u: -u,          # plain rounding
+             1.0 / 3.0: 349525 * u, -1234.5: -1234.5}
+    e = np.array(list(cases))
+    got = o.grid20(e)
+    assert np.array_equal(got, np.array(list(cases.values()))), (e, got)
+    assert np.signbit(o.grid20([-0.5 * u])[0]) or o.grid20([-0.5 * u])[0] == 0.0
+    rng = np.random.default_rng(20)
+    r = np.concatenate([rng.normal(0, 3, 2000), rng.normal(0, 1e4, 500),
+                        (rng.integers(-2**30, 2**30, 500) + 0.5) * u])   # many exact ties
+    want = np.array([nearest_multiple_2m20(float(x)) for x in r])
+    assert np.array_equal(o.grid20(r), want)
+
+
+def test_grid20_is_round_to_nearest_multiple_of_2m20_ties_even():
+    check_grid20(pf_oracle.default())
+
+
+def check_quantised_weights(o):
+    """q_i = floor(2^32 exp(e_i - max e)); with the state-dependent variance,
+    from the rounded log-weights.  Exact facts: the maximal particle gets 2^32
+    in either mode (also when max e is off the grid); two log-weights in the
+    same 2^-20 cell get equal weights only in the rounded mode; exp(-2^-23)
+    rounds to 1 - 2^-23 + 2^-47, so its weight is 2^32 - 512."""
+    e = np.array([-1.0, -1.0 - 2.0 ** -23])
+    assert list(o.quantise_weights(e, svar=False)) == [2**32, 2**32 - 512]
+    assert list(o.quantise_weights(e, svar=True)) == [2**32, 2**32]
+    off = np.array([-1.0 / 3.0, -0.3, -2.0])              # maximum -0.3, off the grid
+    for svar in (False, True):
+        q = o.quantise_weights(off, svar=svar)
+        assert q[1] == 2**32 and q[0] < 2**32 and q[2] < q[0]
+    q = o.quantise_weights(np.array([0.0, np.log(0.5)]), svar=False)
+    assert q[0] == 2**32 and q[1] in (2**31, 2**31 - 1)
+    # the first maximum in particle order is the reference
+    assert list(o.quantise_weights(np.array([-0.5, -0.5]), svar=True)) == [2**32, 2**32]
+
+
+def test_quantised_resampling_weights():
+    check_quantised_weights(pf_oracle.default())
