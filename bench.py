@@ -290,8 +290,8 @@ def run_reference_exact(a) -> None:
     print(json.dumps({
         "impl": "reference", "metric": metric, "mode": a.mode, "value": value,
         "unit": "theta-likelihoods/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
-        "ms_per_step": 1e3 * w.M / value if value > 0 else None, "higher_is_better": True,
-        "dtype": "f64", "data": "synthetic", "config": config,
+        "ms_per_step": 1e3 * w.M / value if value > 0 else None, "ms_per_step_extrapolated": True,
+        "higher_is_better": True, "dtype": "f64", "data": "synthetic", "config": config,
         "cpu_baseline": {k: last[k] for k in ("kind", "cores", "sample")} | {"value": value,
                                                                            "unit": last["unit"]},
         "e2e": {"value": value, "unit": "theta-likelihoods/s", "h2d_bytes_per_step": 0,
@@ -319,6 +319,7 @@ def run_reference(a, rank: int) -> None:
         "metric": "theta-likelihoods/s", "value": value, "unit": "theta-likelihoods/s",
         "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": 1e3 * w.M / value if value > 0 else None,
+        "ms_per_step_extrapolated": True,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_of(w),
         "cpu_baseline": {k: last[k] for k in ("kind", "cores", "sample")} | {"value": value,
@@ -375,6 +376,11 @@ def main() -> None:
     ap.add_argument("--max-theta", type=int, default=0,
                     help="profiling case: only the first M' theta rows (not a bench line)")
     ap.add_argument("--no-probe", action="store_true")
+    ap.add_argument("--no-phases", action="store_true",
+                    help="skip the extra launch that measures the per-phase shares")
+    ap.add_argument("--particles", type=int, default=0,
+                    help="particles per filter instead of the workload's N (not the contract's "
+                         "workload: e.g. a population beyond shared memory)")
     ap.add_argument("--probe-only", action="store_true",
                     help="run the FP64 cost probe alone and print it")
     ap.add_argument("--mode", default="step", choices=["step", "hetero", "serve", "fsp", "ode"],
@@ -432,6 +438,8 @@ def main() -> None:
         a.cluster = CLUSTER_BLOCKS.get(a.workload, 0)
     if a.max_theta:
         w.M = min(w.M, a.max_theta)
+    if a.particles:
+        w.N = a.particles
     th_np = np.ascontiguousarray(multi.rank_thetas(w, rank)[: w.M])
     y_np = w.observations()
     th = torch.from_numpy(th_np).to(dev)
@@ -507,6 +515,22 @@ def main() -> None:
         assert np.array_equal(host_out["loglik"], out["loglik"].cpu().numpy())
     e2e_s = multi.max_over_ranks(float(np.mean(e2e_times)) if e2e_times else float("nan"), dev)
 
+    # where a filter's time goes: one more launch with the per-phase clocks,
+    # outside the timed region (one block per filter only)
+    phases = None
+    if a.cluster <= 1 and not a.no_phases:
+        ph = pf.pf_loglik(w.net, th, w.x0, w.obs_times, yd, w.C, w.sigma, w.N, w.filter_seed,
+                          stream=stream.cuda_stream, model=w.model, phase_cycles=True,
+                          **{k: v for k, v in launch.items() if k != "cluster_blocks"})
+        torch.cuda.synchronize()
+        ok = (ph["status"] == 0).cpu().numpy()
+        cyc = ph["phase_cycles"].cpu().numpy().astype(np.float64)[ok].sum(axis=(0, 1))
+        tot = float(cyc.sum())
+        phases = {"resample_gather": cyc[0] / tot, "simulation": cyc[1] / tot,
+                  "weights_increment": cyc[2] / tot,
+                  "how": "SM clock64 cycles of each filter block per phase (thread 0, phases end "
+                         "at block barriers), summed over the finished filters of one extra launch"}
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = oracle_baseline(a.workload, a.cpu_seconds)
@@ -542,6 +566,7 @@ def main() -> None:
                                         "152 SMs x 2070 MHz",
                          "kernel_ms": local_ms},
             "fp64_probe": probe,
+            "phase_share": phases,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

@@ -153,6 +153,11 @@ typedef struct {
  *                 Rows with equal (theta row, theta id) get equal results
  *                 wherever they sit, so rows a..b of a batch evaluated alone
  *                 with theta_ids = a..b reproduce the whole batch's rows.
+ *   phase_cycles  optional [M][T][3] uint64: SM clock cycles each filter's
+ *                 block spent in resampling + gather, in the simulation, and
+ *                 in the weights + likelihood increment, summed over its
+ *                 intervals (measurement support; one block per filter only,
+ *                 PF_EINVAL with cluster_blocks > 1).
  *   Diagnostics are defined only for filters whose status is PF_ST_OK.
  */
 /*
@@ -212,6 +217,7 @@ typedef struct {
     const pf_model *model;
     int32_t cluster_blocks;
     const uint32_t *theta_ids;
+    uint64_t *phase_cycles;
 } pf_options;
 
 /*

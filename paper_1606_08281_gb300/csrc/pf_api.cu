@@ -276,6 +276,7 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
         if (cs + pf::filter_static_smem() > (size_t)smem_max)
             return fail(PF_EINVAL, "a %d-block cluster's share of %d particles does not fit in shared memory", CB, N);
         if (M * (int64_t)T * CB > 0x7FFFFFFFll) return fail(PF_EINVAL, "M * T * cluster_blocks must be < 2^31");
+        if (o.phase_cycles) return fail(PF_EINVAL, "phase_cycles needs one block per filter (cluster_blocks <= 1)");
         a.cluster = CB;
     }
 
@@ -320,6 +321,8 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
     PF_CUDA(pick(o.events, b_evf, sizeof(uint64_t) * F, &p), "alloc events"); a.ev_f = (uint64_t *)p;
     if (o.digest) { PF_CUDA(pick(o.digest, b_dgf, sizeof(uint64_t) * F, &p), "alloc digest"); a.dg_f = (uint64_t *)p; }
     if (o.final_states) { PF_CUDA(pick(o.final_states, b_fs, n_fs, &p), "alloc final_states"); a.final_states = (int32_t *)p; }
+    DevBuf b_ph;
+    if (o.phase_cycles) { PF_CUDA(pick(o.phase_cycles, b_ph, sizeof(uint64_t) * 3 * F, &p), "alloc phase_cycles"); a.phase_f = (uint64_t *)p; }
 
     DevBuf b_cost, b_order;
     // AUTO keeps row order: on a uniform-prior batch an unconditioned pilot path
@@ -378,6 +381,7 @@ int pf_loglik(const pf_network *net, const double *thetas, int64_t M, int32_t d,
         if (o.events) PF_CUDA(cudaMemcpyAsync(o.events, a.ev_f, sizeof(uint64_t) * F, cudaMemcpyDeviceToHost, s), "copy events");
         if (o.digest) PF_CUDA(cudaMemcpyAsync(o.digest, a.dg_f, sizeof(uint64_t) * F, cudaMemcpyDeviceToHost, s), "copy digest");
         if (o.final_states) PF_CUDA(cudaMemcpyAsync(o.final_states, a.final_states, n_fs, cudaMemcpyDeviceToHost, s), "copy final_states");
+        if (o.phase_cycles) PF_CUDA(cudaMemcpyAsync(o.phase_cycles, a.phase_f, sizeof(uint64_t) * 3 * F, cudaMemcpyDeviceToHost, s), "copy phase_cycles");
         PF_CUDA(cudaStreamSynchronize(s), "synchronize");
     }
     return PF_OK;

@@ -145,6 +145,7 @@ batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *ite
         job.ev_out = ev_f + f;
         job.dg_out = nullptr;
         job.fs_out = nullptr;
+        job.ph_out = nullptr;
         job.acc = rq.acc ? rq.acc + row : nullptr;
         job.reject_below = rq.reject_below;
         job.slack = rq.slack;

@@ -627,6 +627,7 @@ struct FilterJob {
     unsigned long long *ev_out;
     unsigned long long *dg_out;  // may be null
     int32_t *fs_out;             // [N][U], may be null
+    unsigned long long *ph_out;  // [3] SM cycles per phase, may be null
     // Early rejection (level-set threshold): acc points at this theta row's
     // running upper bound of its log-likelihood, shared by its trajectories'
     // filters (null: off).  Each interval adds (increment - slack), where
@@ -677,9 +678,15 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
     __syncthreads();
     unsigned long long fired = 0, dig = 0;
     double t_prev = 0.0;
+    // optional phase clocks (thread 0; the phases end at block barriers):
+    // resampling + gather, simulation, weights + increment
+    const bool want_ph = job.ph_out != nullptr && tid == 0;
+    unsigned long long ph[3] = {0ull, 0ull, 0ull};
+    long long c_mark = 0;
 
     for (int k = 0; k < K; ++k) {
         const uint32_t lane = (static_cast<uint32_t>(traj) << 20) | static_cast<uint32_t>(k);
+        if (want_ph) c_mark = clock64();
         if (job.acc) {  // another trajectory of this theta may already have pushed the bound below
             if (tid == 0 && *reinterpret_cast<volatile double *>(job.acc) < job.reject_below)
                 sh.status = PF_ST_REJECTED;
@@ -727,6 +734,11 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
         } else if (want_digest) {
             for (int j = tid; j < N; j += B) anc[j] = j;
         }
+        if (want_ph) {
+            const long long c = clock64();
+            ph[0] += static_cast<unsigned long long>(c - c_mark);
+            c_mark = c;
+        }
 
         const double t_k = job.obs_times[k];
         if (t_k > t_prev) {
@@ -744,6 +756,11 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
                                  job.budget, fired);
         }
         __syncthreads();
+        if (want_ph) {
+            const long long c = clock64();
+            ph[1] += static_cast<unsigned long long>(c - c_mark);
+            c_mark = c;
+        }
         if (sh.status != PF_ST_OK) break;
 
         if (want_digest)
@@ -791,6 +808,7 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
                     sh.status = PF_ST_REJECTED;
             }
         }
+        if (want_ph) ph[2] += static_cast<unsigned long long>(clock64() - c_mark);
         t_prev = t_k;
     }
     __syncthreads();
@@ -802,6 +820,8 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
         *job.st_out = static_cast<uint8_t>(status);
         *job.ev_out = fired_all;
         if (job.dg_out) *job.dg_out = dig_all;
+        if (want_ph)
+            for (int i = 0; i < 3; ++i) job.ph_out[i] = ph[i];
     }
     if (job.fs_out && status == PF_ST_OK) {
         for (int j = tid; j < N; j += B)

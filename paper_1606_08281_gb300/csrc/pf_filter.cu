@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(128, 4) filter_kernel(const FilterArgs args) {
     job.dg_out = args.dg_f ? reinterpret_cast<unsigned long long *>(args.dg_f) + f : nullptr;
     job.fs_out = args.final_states ? args.final_states + f * static_cast<int64_t>(args.N) * args.net.U
                                    : nullptr;
+    job.ph_out = args.phase_f ? reinterpret_cast<unsigned long long *>(args.phase_f) + 3 * f : nullptr;
     job.acc = args.acc ? args.acc + mrow : nullptr;
     job.reject_below = args.reject_below;
     job.slack = args.slack;
@@ -117,6 +118,7 @@ __global__ void __launch_bounds__(128, 4) filter_kernel_cluster(const FilterArgs
     job.dg_out = args.dg_f ? reinterpret_cast<unsigned long long *>(args.dg_f) + f : nullptr;
     job.fs_out = args.final_states ? args.final_states + f * static_cast<int64_t>(args.N) * args.net.U
                                    : nullptr;
+    job.ph_out = args.phase_f ? reinterpret_cast<unsigned long long *>(args.phase_f) + 3 * f : nullptr;
     job.acc = args.acc ? args.acc + mrow : nullptr;
     job.reject_below = args.reject_below;
     job.slack = args.slack;
@@ -165,6 +167,8 @@ __global__ void __launch_bounds__(128, 4) filter_kernel_global(const FilterArgs 
         job.fs_out = args.final_states
                          ? args.final_states + f * static_cast<int64_t>(args.N) * args.net.U
                          : nullptr;
+        job.ph_out = args.phase_f ? reinterpret_cast<unsigned long long *>(args.phase_f) + 3 * f
+                                  : nullptr;
         job.acc = args.acc ? args.acc + mrow : nullptr;
         job.reject_below = args.reject_below;
         job.slack = args.slack;

@@ -57,6 +57,7 @@ struct FilterArgs {
     uint64_t *ev_f;
     uint64_t *dg_f;          // may be null: digest not computed
     int32_t *final_states;   // [M*T][N][U], may be null
+    uint64_t *phase_f;       // [M*T][3] SM cycles per phase, may be null
     const uint32_t *row_order;  // [M] theta rows in launch order (null: 0..M-1)
     const uint32_t *theta_ids;  // [M] theta id of each row in the random-number counter (null: m)
     double *acc;                // [M] running upper bounds for early rejection (null: off)

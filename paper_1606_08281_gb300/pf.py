@@ -66,7 +66,8 @@ class pf_options(ct.Structure):
                 ("final_states", ct.c_void_p), ("schedule", ct.c_int32),
                 ("early_reject", ct.c_int32), ("row_order", ct.c_void_p),
                 ("reject_below", ct.c_double), ("model", ct.POINTER(pf_model)),
-                ("cluster_blocks", ct.c_int32), ("theta_ids", ct.c_void_p)]
+                ("cluster_blocks", ct.c_int32), ("theta_ids", ct.c_void_p),
+                ("phase_cycles", ct.c_void_p)]
 
 
 class pf_fsp_options(ct.Structure):
@@ -219,13 +220,16 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
               event_budget: int = 0, block_threads: int = 0, stream=None,
               diagnostics: bool = False, final_states: bool = False, out=None,
               schedule: int = PF_SCHED_AUTO, row_order=None, reject_below=None,
-              model: dict | None = None, cluster_blocks: int = 0, theta_ids=None):
+              model: dict | None = None, cluster_blocks: int = 0, theta_ids=None,
+              phase_cycles: bool = False):
     """Log-likelihood of every theta row (see pf_loglik in include/pf1606.h).
 
     model: optional Lac-Gfp extensions {"rate_coef", "x0_hi", "obs_offset",
     "obs_var"} (pf_model; host arrays).
     cluster_blocks: 2..8 splits each filter over a thread-block cluster of
     that many blocks (pf_options.cluster_blocks); 0 = one block per filter.
+    phase_cycles: also return 'phase_cycles' [M][T][3], the SM cycles each
+    filter spent in resampling + gather, simulation, weights + increment.
     theta_ids: optional [M] uint32 theta ids of the rows in the random-number
     counter (pf_options.theta_ids; default 0..M-1), in the memory space of
     `thetas` (a uint32-valued CUDA tensor of dtype int32 in device mode).
@@ -259,6 +263,8 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
             if final_states:
                 out["final_states"] = torch.empty((M, T, n_particles, U), dtype=torch.int32,
                                                   device=dev)
+            if phase_cycles:
+                out["phase_cycles"] = torch.empty((M, T, 3), dtype=torch.int64, device=dev)
         if stream is None:
             stream = torch.cuda.current_stream(dev).cuda_stream
         ptr = lambda k: (out[k].data_ptr() if k in out else None)  # noqa: E731
@@ -279,6 +285,8 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
                 out["digest"] = np.empty((M, T), np.uint64)
             if final_states:
                 out["final_states"] = np.empty((M, T, n_particles, U), np.int32)
+            if phase_cycles:
+                out["phase_cycles"] = np.empty((M, T, 3), np.uint64)
         ptr = lambda k: (out[k].ctypes.data if k in out else None)  # noqa: E731
         p_th, p_ts, p_y = _hptr(th), _hptr(ts), _hptr(yy)
     Ch = _host(C, np.float64).reshape(P, U)
@@ -310,7 +318,7 @@ def pf_loglik(net: dict, thetas, x0, obs_times, y, C, sigma, n_particles: int, s
                      stream if device else None, ptr("ll_traj"), ptr("events"), ptr("digest"),
                      ptr("final_states"), int(schedule), 0 if reject_below is None else 1, p_ro,
                      float("nan") if reject_below is None else float(reject_below), mdl.ptr(),
-                     int(cluster_blocks), p_ids)
+                     int(cluster_blocks), p_ids, ptr("phase_cycles"))
     rc = lib.pf_loglik(ct.byref(n.s), p_th, M, d, _hptr(x0h), p_ts, K, p_y, T, P, _hptr(Ch),
                        _hptr(sg), int(n_particles), ct.c_uint64(int(seed) & (2**64 - 1)),
                        ptr("loglik"), ptr("status"), ct.byref(opt))

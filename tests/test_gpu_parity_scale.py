@@ -91,9 +91,9 @@ def account(bad: np.ndarray, trace=None):
 
 def tracer(pf, w, thetas, ids, N, seed, times, y, cluster_blocks=0):
     """First-divergence trace of filter (row m, trajectory t) of a case."""
-    from tests import divergence
 
     def trace(m, t):
+        from tests import divergence
         return divergence.trace_filter(pf, w.net, thetas[m], int(ids[m]), t, w.x0, times, y, w.C,
                                        w.sigma, N, seed, model=w.model,
                                        cluster_blocks=cluster_blocks)
