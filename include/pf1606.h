@@ -550,6 +550,16 @@ int pf_exp_variates(uint64_t seed, int64_t n, double *out);
  */
 int pf_div_check(uint64_t seed, int64_t n, uint64_t *mismatches);
 
+/*
+ * pf_convert_check -- test support for the kernels' conversion of a
+ * propensity's combinatorial count h >= 0 to double (integer operations only,
+ * rounded to nearest even above 2^53): over n pseudo-random counts spread over
+ * every magnitude up to 2^62 (ties and near ties of the rounding included),
+ * counts the conversions that differ from the IEEE conversion.  Synchronous.
+ * PF_OK, PF_EINVAL, PF_ENOMEM or PF_ECUDA.
+ */
+int pf_convert_check(uint64_t seed, int64_t n, uint64_t *mismatches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -108,11 +108,13 @@ def _paths_rows(task: dict) -> np.ndarray:
 
 
 def path_events(net, thetas, x0, times, seed: int, rows_per_task: int = 256,
-                processes: int | None = None) -> np.ndarray:
+                processes: int | None = None, rate_coef=None) -> np.ndarray:
     """Events of one oracle SSA path per theta row over `times` (a cost
-    ranking of the rows for choosing test cases; not a filter result)."""
+    ranking of the rows for choosing test cases; not a filter result).
+    rate_coef [R][d] composes the rates as in the model extensions."""
     thetas = np.asarray(thetas, np.float64)
-    tasks = [dict(net=net, thetas=thetas[i:i + rows_per_task], x0=x0, times=times, seed=seed)
+    tasks = [dict(net=net, thetas=thetas[i:i + rows_per_task], x0=x0, times=times, seed=seed,
+                  rate_coef=rate_coef)
              for i in range(0, len(thetas), rows_per_task)]
     n = min(len(tasks), processes or os.cpu_count() or 1)
     if n <= 1:

@@ -152,14 +152,14 @@ __device__ __forceinline__ long long dbits(double x) { return __double_as_longlo
 
 // Simulate every particle of the filter from t_prev to t_end by Gillespie's
 // direct method (Supp. I, "Simulate X_t"; Sec. "The stochastic birth-death
-// Model": SSA).  Lanes take particles from a pool in the order `order`; each
+// Model": SSA).  Lanes take particle slots from a pool in index order; each
 // loop trip is one direct-method step of every active lane.  Failure is
 // reported through sh.status (PF_ST_BUDGET when a particle needed more than
 // `budget` draws); `fired` counts reactions.  Particle slot j of `xs` is
 // particle j0 + j of the filter (j0 > 0 when the filter is split over the
 // blocks of a cluster); the random stream is keyed by the latter.
 template <int RM, int UM>
-__device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, int N,
+__device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N,
                              double t_prev, double t_end, uint32_t key0, uint32_t key1,
                              uint32_t lane, uint32_t mrow, uint64_t budget,
                              unsigned long long &fired, uint32_t j0 = 0) {
@@ -185,7 +185,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
     auto take = [&](bool &act) {
         const int slot = atomicAdd(&sh.pool_next, 1);
         act = slot < N;
-        L.j = act ? order[slot] : 0;
+        L.j = act ? slot : 0;
         load_x(act);
     };
     double a[RM], S[RM];
@@ -260,6 +260,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
             const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
             double E;
             const bool fast = zig_fast(r0, sh.zig.x, E);
+            int first_dep = 0;  // dependency lists: the first propensity this step recomputes
             if constexpr (kDepList || kHoist) {
                 // Each lane recomputes its own list of propensities: the fired
                 // reaction's dependents, or (a particle just taken from the
@@ -300,6 +301,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                         const int r = lst[i];
                         a[r] = propensity<UM>(r, sh, L);
                     }
+                    first_dep = refill ? 0 : (nd > 0 ? lst[0] : R);
                 }
             } else {
                 // mid-size networks with the state in shared memory: the
@@ -315,14 +317,28 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, const int *order, int Np, 
                     }
                 }
             }
-            double run = a[0];
-            S[0] = run;
+            double run;
             if constexpr (kDepList) {
-                for (int r = 1; r < R; ++r) {
+                // The prefix sums below the earliest recomputed propensity of
+                // any lane of the warp are unchanged since the previous step
+                // (the same additions of the same values), so the warp re-adds
+                // from there on: exact, and a uniform trip count.
+                const int fw = static_cast<int>(__reduce_min_sync(busy, static_cast<unsigned>(first_dep)));
+                int r1 = fw;
+                if (fw == 0) {
+                    run = a[0];
+                    S[0] = run;
+                    r1 = 1;
+                } else {
+                    run = S[fw - 1];
+                }
+                for (int r = r1; r < R; ++r) {
                     run = __dadd_rn(run, a[r]);
                     S[r] = run;
                 }
             } else {
+                run = a[0];
+                S[0] = run;
 #pragma unroll
                 for (int r = 1; r < RM; ++r) {
                     if (r < R) run = __dadd_rn(run, a[r]);
@@ -742,18 +758,17 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
 
         const double t_k = job.obs_times[k];
         if (t_k > t_prev) {
-            // pool order: the particles in index order (the refill loop and the
-            // tail consolidation absorb their unequal costs; sorting them
-            // heaviest first no longer paid for its two passes)
+            // the pool hands out particle slots in index order (the refill
+            // loop and the tail consolidation absorb their unequal costs;
+            // sorting them heaviest first no longer paid for its two passes)
             if (tid == 0) {
                 sh.pool_next = 0;
                 sh.rem_n[0] = 0;
                 sh.rem_n[1] = 0;
             }
-            for (int j = tid; j < N; j += B) order[j] = j;
             __syncthreads();
-            ssa_interval<RM, UM>(sh, xs, order, Np, N, t_prev, t_k, key0, key1, lane, m32,
-                                 job.budget, fired);
+            ssa_interval<RM, UM>(sh, xs, Np, N, t_prev, t_k, key0, key1, lane, m32, job.budget,
+                                 fired);
         }
         __syncthreads();
         if (want_ph) {
@@ -954,10 +969,9 @@ __device__ void run_filter_cluster(const FilterJob &job, SharedHead &sh, unsigne
                 sh.rem_n[0] = 0;
                 sh.rem_n[1] = 0;
             }
-            for (int jl = tid; jl < n; jl += B) order[jl] = jl;
             __syncthreads();
-            ssa_interval<RM, UM>(sh, xs, order, Np, n, t_prev, t_k, key0, key1, lane, m32,
-                                 job.budget, fired, static_cast<uint32_t>(j0));
+            ssa_interval<RM, UM>(sh, xs, Np, n, t_prev, t_k, key0, key1, lane, m32, job.budget,
+                                 fired, static_cast<uint32_t>(j0));
         }
         __syncthreads();
 

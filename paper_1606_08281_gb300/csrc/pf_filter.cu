@@ -404,11 +404,12 @@ int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, v
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t smem = filter_smem_bytes(a.N, a.net.U, a.dg_f != nullptr);
     int e;
-    const bool small_u = a.net.U <= 4;
+    const bool small_u = a.net.U <= 4, tiny_u = a.net.U <= 2;
     if (slabs) {
         switch (reaction_tier(a.net.R)) {
-            case 4: e = small_u ? launch_tier_global<4, 4>(a, B, slabs, slab_bytes, grid, s)
-                                : launch_tier_global<4, 0>(a, B, slabs, slab_bytes, grid, s); break;
+            case 4: e = tiny_u ? launch_tier_global<4, 2>(a, B, slabs, slab_bytes, grid, s)
+                    : small_u ? launch_tier_global<4, 4>(a, B, slabs, slab_bytes, grid, s)
+                              : launch_tier_global<4, 0>(a, B, slabs, slab_bytes, grid, s); break;
             case 8: e = small_u ? launch_tier_global<8, 4>(a, B, slabs, slab_bytes, grid, s)
                                 : launch_tier_global<8, 0>(a, B, slabs, slab_bytes, grid, s); break;
             case 16: e = launch_tier_global<16, 0>(a, B, slabs, slab_bytes, grid, s); break;
@@ -418,15 +419,17 @@ int launch_filter(const FilterArgs &a, int B, double *loglik, uint8_t *status, v
         const int C = a.cluster;
         const size_t cs = cluster_smem_bytes(a.N, C, a.net.U, a.dg_f != nullptr);
         switch (reaction_tier(a.net.R)) {
-            case 4: e = small_u ? launch_tier_cluster<4, 4>(a, B, cs, C, s)
-                                : launch_tier_cluster<4, 0>(a, B, cs, C, s); break;
+            case 4: e = tiny_u ? launch_tier_cluster<4, 2>(a, B, cs, C, s)
+                    : small_u ? launch_tier_cluster<4, 4>(a, B, cs, C, s)
+                              : launch_tier_cluster<4, 0>(a, B, cs, C, s); break;
             case 8: e = small_u ? launch_tier_cluster<8, 4>(a, B, cs, C, s)
                                 : launch_tier_cluster<8, 0>(a, B, cs, C, s); break;
             case 16: e = launch_tier_cluster<16, 0>(a, B, cs, C, s); break;
             default: e = launch_tier_cluster<32, 0>(a, B, cs, C, s); break;
         }
     } else switch (reaction_tier(a.net.R)) {
-        case 4: e = small_u ? launch_tier<4, 4>(a, B, smem, s) : launch_tier<4, 0>(a, B, smem, s); break;
+        case 4: e = tiny_u ? launch_tier<4, 2>(a, B, smem, s)
+                : small_u ? launch_tier<4, 4>(a, B, smem, s) : launch_tier<4, 0>(a, B, smem, s); break;
         case 8: e = small_u ? launch_tier<8, 4>(a, B, smem, s) : launch_tier<8, 0>(a, B, smem, s); break;
         case 16: e = launch_tier<16, 0>(a, B, smem, s); break;
         default: e = launch_tier<32, 0>(a, B, smem, s); break;

@@ -206,3 +206,47 @@ extern "C" int pf_div_check(uint64_t seed, int64_t n, uint64_t *mismatches) {
     *mismatches = h;
     return e == cudaSuccess ? PF_OK : PF_ECUDA;
 }
+
+namespace {
+// Counts the conversions where count_to_double(h) differs from the IEEE
+// conversion of h, over n pseudo-random counts h >= 0 whose magnitudes spread
+// over 0 .. 2^62 (every exponent), half of them exact (< 2^53) and half
+// rounded, plus the rounding cases built on purpose: the low bits just below,
+// at and above one half, with even and odd significands.
+__global__ void convert_check_kernel(uint64_t seed, int64_t n, unsigned long long *mismatch) {
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    unsigned long long local = 0;
+    for (int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; k < n; k += stride) {
+        const pf::Philox4 w = pf::philox4x32_10(static_cast<uint32_t>(k), static_cast<uint32_t>(k >> 32),
+                                                0xC0u, 0u, static_cast<uint32_t>(seed),
+                                                static_cast<uint32_t>(seed >> 32));
+        const uint64_t r = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+        const int bits = static_cast<int>(w.w2 % 63u);                  // magnitude below 2^bits
+        uint64_t h = bits ? (r >> (64 - bits)) : 0ull;
+        if ((w.w3 & 3u) == 0u && bits > 53) {                          // a tie or a near tie
+            const int drop = bits - 53;
+            const uint64_t halfway = 1ull << (drop - 1);
+            const int64_t off = static_cast<int64_t>((w.w3 >> 2) % 3u) - 1;     // -1, 0, +1
+            h = (h & ~((1ull << drop) - 1ull)) |
+                static_cast<uint64_t>(static_cast<int64_t>(halfway) + off);
+        }
+        const long long hv = static_cast<long long>(h);
+        if (__double_as_longlong(pf::count_to_double(hv)) != __double_as_longlong(__ll2double_rn(hv)))
+            ++local;
+    }
+    if (local) atomicAdd(mismatch, local);
+}
+}  // namespace
+
+extern "C" int pf_convert_check(uint64_t seed, int64_t n, uint64_t *mismatches) {
+    if (n < 0 || !mismatches) return PF_EINVAL;
+    unsigned long long *d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned long long)) != cudaSuccess) return PF_ENOMEM;
+    cudaMemset(d, 0, sizeof(unsigned long long));
+    convert_check_kernel<<<152 * 8, 256>>>(seed, n, d);
+    unsigned long long h = 0;
+    cudaError_t e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    *mismatches = h;
+    return e == cudaSuccess ? PF_OK : PF_ECUDA;
+}

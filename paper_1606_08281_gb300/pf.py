@@ -31,7 +31,7 @@ EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philo
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",
             "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit", "pf_poll", "pf_ctx_stats",
             "pf_ctx_destroy", "pf_exp_variates", "pf_div_check", "pf_ctx_load_problem_model",
-            "pf_fsp_loglik", "pf_erk_loglik"]
+            "pf_fsp_loglik", "pf_erk_loglik", "pf_convert_check"]
 
 
 class PfError(RuntimeError):
@@ -139,6 +139,8 @@ def load():
             lib.pf_exp_variates.restype = ct.c_int
             lib.pf_div_check.argtypes = [ct.c_uint64, ct.c_int64, ct.POINTER(ct.c_uint64)]
             lib.pf_div_check.restype = ct.c_int
+            lib.pf_convert_check.argtypes = [ct.c_uint64, ct.c_int64, ct.POINTER(ct.c_uint64)]
+            lib.pf_convert_check.restype = ct.c_int
             lib.pf_loglik_noalloc.argtypes = [ct.POINTER(pf_network), P, ct.c_int64, ct.c_int32,
                                               P, P, ct.c_int32, P, ct.c_int32, ct.c_int32, P, P,
                                               ct.c_int32, ct.c_uint64, P, P, ct.c_uint64, P]
@@ -469,6 +471,14 @@ def pf_div_check(seed: int, n: int) -> int:
     lib = load()
     m = ct.c_uint64()
     _check(lib.pf_div_check(ct.c_uint64(int(seed)), int(n), ct.byref(m)), "pf_div_check")
+    return int(m.value)
+
+
+def pf_convert_check(seed: int, n: int) -> int:
+    """Number of the kernels' count-to-double conversions differing from IEEE."""
+    lib = load()
+    m = ct.c_uint64()
+    _check(lib.pf_convert_check(ct.c_uint64(int(seed)), int(n), ct.byref(m)), "pf_convert_check")
     return int(m.value)
 
 

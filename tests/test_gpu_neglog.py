@@ -81,3 +81,10 @@ def test_waiting_time_division_matches_ieee(pf):
     rounding midpoint) and the Gaussian weight's (y - mu) / sigma from the
     correctly rounded 1 / sigma (exact by Markstein's theorem)."""
     assert pf.pf_div_check(7, 100_000_000) == 0
+
+
+def test_count_conversion_matches_ieee(pf):
+    """The kernels convert propensity counts to double with integer operations
+    only: equal to the IEEE conversion on 10^8 counts of every magnitude,
+    rounding cases included."""
+    assert pf.pf_convert_check(11, 100_000_000) == 0

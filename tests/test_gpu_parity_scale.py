@@ -15,12 +15,16 @@ batch.  Cases (filters):
     25 filter seeds: 5 000;
   * gene expression, every row and trajectory of the full workload (4096 x 10)
     at N = 100 over the full 50 times: 40 960;
-  * gene expression at full size (N = 1000): the six heaviest rows of the
-    top decile by a host cost proxy, all 10 trajectories, from the full
-    4096-row launch the benchmark times: 60;
+  * gene expression at full size (N = 1000): the two heaviest rows by a host
+    cost proxy and ten more of its top decile, all 10 trajectories, from the
+    full 4096-row launch the benchmark times: 120;
   * the cascade at full size (16 trajectories x 512 particles x 100 times): the
-    three heaviest rows by an oracle pilot path over all 16 384 rows, plus
-    three random rows, run on the GPU with their ids: 96.
+    five heaviest rows by an oracle pilot path over all 16 384 rows, plus five
+    random rows, run on the GPU with their ids: 160;
+  * Lac-Gfp at full size (4 trajectories x 200 particles x 29 times, each
+    filter split over a 4-block cluster as the benchmark runs it): the twelve
+    lightest rows by an oracle pilot path (its heaviest filters fire 10^9
+    reactions, beyond the oracle's reach in a test): 48.
 """
 from __future__ import annotations
 
@@ -158,7 +162,7 @@ def test_gene_expression_full_size_heaviest_rows(pf):
     order = np.argsort(-cost)
     decile = order[: len(th) // 10]
     rng = np.random.default_rng(2718)
-    pick = np.unique(np.concatenate([decile[:2], rng.choice(decile[2:], 4, replace=False)]))
+    pick = np.unique(np.concatenate([decile[:2], rng.choice(decile[2:], 10, replace=False)]))
     tasks, where = pool.filter_tasks(w.net, th[pick], pick, w.x0, w.obs_times, w.observations(),
                                      w.C, w.sigma, w.N, w.filter_seed, split_trajectories=True)
     o = pool.assemble(pool.map_loglik(tasks), where, len(pick), w.T)
@@ -173,16 +177,16 @@ def test_gene_expression_full_size_heaviest_rows(pf):
 
 def test_cascade_full_horizon_heaviest_rows(pf):
     """The 10-species cascade at its full per-filter size (16 trajectories x
-    512 particles x 100 times): three heaviest rows of the 16 384 by one
-    oracle pilot path each, plus three random rows, launched on the GPU with
-    their ids (one block per filter, as the benchmark runs it)."""
+    512 particles x 100 times): five heaviest rows of the 16 384 by one oracle
+    pilot path each, plus five random rows, launched on the GPU with their ids
+    (one block per filter, as the benchmark runs it)."""
     w = W.cascade()
     th = w.thetas()
     pilot = pool.path_events(w.net, th, w.x0, w.obs_times, seed=99)
     order = np.argsort(-pilot.astype(np.int64))
     rng = np.random.default_rng(3141)
-    rest = np.setdiff1d(np.arange(len(th)), order[:3])
-    pick = np.unique(np.concatenate([order[:3], rng.choice(rest, 3, replace=False)]))
+    rest = np.setdiff1d(np.arange(len(th)), order[:5])
+    pick = np.unique(np.concatenate([order[:5], rng.choice(rest, 5, replace=False)]))
     g = pf.pf_loglik(w.net, th[pick], w.x0, w.obs_times, w.observations(), w.C, w.sigma, w.N,
                      w.filter_seed, diagnostics=True, theta_ids=pick)
     tasks, where = pool.filter_tasks(w.net, th[pick], pick, w.x0, w.obs_times, w.observations(),
@@ -192,3 +196,24 @@ def test_cascade_full_horizon_heaviest_rows(pf):
     assert int(np.asarray(g["events"]).sum()) > 10**8
     account(bad, tracer(pf, w, th[pick], pick, w.N, w.filter_seed, w.obs_times,
                         w.observations()))
+
+
+def test_lac_gfp_full_size_light_rows(pf):
+    """The paper's Lac-Gfp network with its model extensions (composed and
+    shared rates, uniform initial counts, state-dependent observation
+    variance) at full per-filter size, split over 4-block clusters."""
+    w = W.lac_gfp()
+    th = w.thetas()
+    pilot = pool.path_events(w.net, th, w.x0, w.obs_times, seed=77, rows_per_task=16,
+                             rate_coef=w.model["rate_coef"])
+    pick = np.sort(np.argsort(pilot.astype(np.int64))[:12])
+    g = pf.pf_loglik(w.net, th[pick], w.x0, w.obs_times, w.observations(), w.C, w.sigma, w.N,
+                     w.filter_seed, diagnostics=True, theta_ids=pick, model=w.model,
+                     cluster_blocks=4)
+    tasks, where = pool.filter_tasks(w.net, th[pick], pick, w.x0, w.obs_times, w.observations(),
+                                     w.C, w.sigma, w.N, w.filter_seed, split_trajectories=True,
+                                     model=w.model)
+    o = pool.assemble(pool.map_loglik(tasks), where, len(pick), w.T)
+    bad = compare(g, o)
+    account(bad, tracer(pf, w, th[pick], pick, w.N, w.filter_seed, w.obs_times,
+                        w.observations(), cluster_blocks=4))
