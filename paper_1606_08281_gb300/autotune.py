@@ -4,7 +4,9 @@ For a problem shape (network tier, species, particles, observation times) it
 times pf_loglik on a sample of theta rows for each candidate block size (lanes
 per filter: 64, 96, 128) and launch order, and keeps the fastest.  Results are
 cached in a JSON file keyed by the shape, so a serving process tunes once.
-Results never depend on these parameters, only the time does.
+Results never depend on these parameters, only the time does: the filters'
+histories are exact integer work, and the weights' sum is taken in chunks of
+32 particles in an order that does not depend on the block size.
 """
 from __future__ import annotations
 

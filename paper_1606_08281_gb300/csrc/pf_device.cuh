@@ -478,21 +478,6 @@ __device__ __forceinline__ double block_max(double v, SharedHead &sh) {
     return sh.bcast_d;
 }
 
-__device__ __forceinline__ double block_sum(double v, SharedHead &sh) {
-    for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh.red_d[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        double x = lane < nw ? sh.red_d[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) x = __dadd_rn(x, __shfl_xor_sync(kFull, x, o));
-        if (lane == 0) sh.bcast_d = x;
-    }
-    __syncthreads();
-    return sh.bcast_d;
-}
-
 __device__ __forceinline__ unsigned long long block_sum_u64(unsigned long long v, SharedHead &sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
@@ -537,6 +522,58 @@ __device__ inline void block_scan_u64(unsigned long long *q, int N, SharedHead &
     __syncthreads();
 }
 
+
+// The weights' sum s = sum_j exp(e_j - emax) over the n particles of wbuf,
+// in an order that does not depend on the block size: the particles form
+// chunks of 32 consecutive slots, each summed by a butterfly over a warp's
+// lanes; lane l of warp 0 then adds the chunk sums l, l + 32, ... in order,
+// and a last butterfly adds the lanes.  The chunk sums are kept in `spare`
+// (int [n], free during this step) as pairs of 32-bit words; one chunk needs
+// no storage.  The same exp() values give the integer weights of the next
+// resampling, written over the log-weights (wbuf and qbuf alias); with a
+// state-dependent variance those come from the log-weights rounded to
+// multiples of 2^-20 (grid20) instead.  Every thread receives s.
+__device__ __forceinline__ double weight_sum(double *wbuf, unsigned long long *qbuf, int *spare,
+                                             int n, double emax, bool svar, SharedHead &sh) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int nchunk = (n + 31) >> 5;
+    const double gmax = grid20(emax);
+    double own = 0.0;    // warp 0, one chunk: the whole sum
+    for (int c = warp; c < nchunk; c += nw) {
+        const int j = (c << 5) + lane;
+        double v = 0.0;
+        if (j < n) {
+            const double e = wbuf[j];
+            v = exp(__dsub_rn(e, emax));
+            const double vq = svar ? exp(__dsub_rn(grid20(e), gmax)) : v;
+            qbuf[j] = __double2ull_rz(__dmul_rn(vq, 4294967296.0));
+        }
+        for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
+        if (nchunk == 1) {
+            own = v;
+        } else if (lane == 0) {
+            const long long b = __double_as_longlong(v);
+            spare[2 * c] = static_cast<int>(b);
+            spare[2 * c + 1] = static_cast<int>(b >> 32);
+        }
+    }
+    __syncthreads();
+    if (warp == 0) {
+        double v = own;
+        if (nchunk > 1) {
+            v = 0.0;
+            for (int c = lane; c < nchunk; c += 32) {
+                const long long b = (static_cast<long long>(spare[2 * c + 1]) << 32) |
+                                    static_cast<unsigned int>(spare[2 * c]);
+                v = __dadd_rn(v, __longlong_as_double(b));
+            }
+            for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_xor_sync(kFull, v, o));
+        }
+        if (lane == 0) sh.bcast_d = v;
+    }
+    __syncthreads();
+    return sh.bcast_d;
+}
 
 // Per-filter set-up by the whole block: the theta row's validity (sh.valid),
 // the Gaussian normaliser, 1 / sigma_p and the reaction rates; ends with a
@@ -798,20 +835,8 @@ __device__ void run_filter(const FilterJob &job, SharedHead &sh, unsigned char *
             break;
         }
         // p(y_k | y_<k) ~ (1/N) sum_j l_j  (Eq. likelihood approx.), in logs;
-        // the same exp() values give the integer weights for the next resampling.
-        // With a state-dependent variance the integer weights come from the
-        // log-weights rounded to multiples of 2^-20 (grid20), the sum from the
-        // exact ones.
-        double lsum = 0.0;
-        const double gmax = grid20(emax);
-        for (int j = tid; j < N; j += B) {
-            const double e = wbuf[j];
-            const double v = exp(__dsub_rn(e, emax));
-            lsum = __dadd_rn(lsum, v);
-            const double vq = svar ? exp(__dsub_rn(grid20(e), gmax)) : v;
-            qbuf[j] = __double2ull_rz(__dmul_rn(vq, 4294967296.0));
-        }
-        const double s = block_sum(lsum, sh);
+        // the same exp() values give the integer weights for the next resampling
+        const double s = weight_sum(wbuf, qbuf, order, N, emax, svar, sh);
         if (tid == 0) {
             double inc = __dadd_rn(emax, log(s));
             inc = __dsub_rn(inc, log(static_cast<double>(N)));
@@ -1009,16 +1034,7 @@ __device__ void run_filter_cluster(const FilterJob &job, SharedHead &sh, unsigne
             status = PF_ST_NONFINITE;
             break;
         }
-        double lsum = 0.0;
-        const double gmax = grid20(emax);
-        for (int jl = tid; jl < n; jl += B) {
-            const double e = wbuf[jl];
-            const double v = exp(__dsub_rn(e, emax));
-            lsum = __dadd_rn(lsum, v);
-            const double vq = svar ? exp(__dsub_rn(grid20(e), gmax)) : v;
-            qbuf[jl] = __double2ull_rz(__dmul_rn(vq, 4294967296.0));
-        }
-        const double bsum = block_sum(lsum, sh);
+        const double bsum = weight_sum(wbuf, qbuf, order, n, emax, svar, sh);
         block_scan_u64(qbuf, n, sh);
         if (tid == 0) {
             sh.cx_lsum = bsum;

@@ -303,3 +303,17 @@ def test_reaction_tiers(pf, kind, N):
     g, o = run_both(pf, net, th, x0, times, y, C, sigma, N, 45, final_states=True)
     assert_parity(g, o, final_states=True)
     assert int(g["events"].sum()) > 1000
+
+
+def test_results_do_not_depend_on_the_block_size(pf):
+    """The weights' sum is taken in chunks of 32 particles in a fixed order, so
+    the log-likelihood (not only the history) is the same bit for bit for every
+    block size, including ragged particle counts."""
+    w = W.gene_expression().subset(T=2, K=6)
+    th = w.thetas(6)
+    for N in (1, 33, 500, 1000):
+        runs = [pf.pf_loglik(w.net, th, w.x0, w.obs_times, w.observations(), w.C, w.sigma, N, 7,
+                             diagnostics=True, block_threads=B) for B in (32, 64, 96, 128)]
+        for r in runs[1:]:
+            assert np.array_equal(r["ll_traj"], runs[0]["ll_traj"]), N
+            assert np.array_equal(r["digest"], runs[0]["digest"]), N
