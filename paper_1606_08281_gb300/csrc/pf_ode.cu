@@ -49,6 +49,8 @@ struct OdeArgs {
     double *ll_f;              // [M * NP]
     uint8_t *st_f;             // [M * NP]
     uint32_t *steps_f;         // [M * NP] or null
+    const int32_t *porder;     // [NP] patterns in the order their problems are handed out
+    unsigned long long *next;  // work counter (zero at launch)
 };
 
 // The reaction equations of the model (Supp. "Reaction Equations"): each pair
@@ -122,9 +124,11 @@ __device__ __forceinline__ void exchange(unsigned pmask, bool h, const double *o
     }
 }
 
-__device__ __forceinline__ double fret(const double *x, const double *th) {
-    const double ERK = x[8], ERKa = x[9], E = th[33];
-    return th[31] * (ERKa * E * th[34] / ((ERK + (1.0 - E) * ERKa) * th[35]) + th[30]);
+// The FRET ratio of state x; fr = (bg, lam, sigma, E, f_AA, f_DD), theta's
+// last six entries.
+__device__ __forceinline__ double fret(const double *x, const double *fr) {
+    const double ERK = x[8], ERKa = x[9], E = fr[3];
+    return fr[1] * (ERKa * E * fr[4] / ((ERK + (1.0 - E) * ERKa) * fr[5]) + fr[0]);
 }
 
 // Dormand-Prince 5(4) tableau.
@@ -140,8 +144,194 @@ constexpr double B1 = 35.0 / 384.0, B3 = 500.0 / 1113.0, B4 = 125.0 / 192.0,
 constexpr double E1 = 71.0 / 57600.0, E3 = -71.0 / 16695.0, E4 = 71.0 / 1920.0,
                  E5 = -17253.0 / 339200.0, E6 = 22.0 / 525.0, E7 = -1.0 / 40.0;
 
-// Threads come in pairs (g = t >> 1), pattern-major (g = p * M + m) so that
-// the lanes of a warp share an input pattern.  Both lanes of a pair take the
+// Threads come in pairs; each pair takes problems (theta row m, input
+// pattern p) from a work counter, pattern by pattern (the patterns with the
+// most input switches, the costliest, first) and, within a pattern, rows in
+// order, so that the pairs of a warp mostly share a pattern and its stop
+// times.  The loop is flat: every trip is one unit of work of every pair -- a
+// new problem's set-up, one Dormand-Prince step, or the log-density at an
+// observation time -- so a pair that finishes its problem takes the next one
+// at once instead of idling until its warp-mates finish theirs, and the last
+// wave has no long tail.  Both lanes of a pair take the same decisions (the
+// error norm is summed over both halves in either order, which is
+// commutative), so they stay converged, and a problem's result depends on its
+// own inputs only: the step sequence is that of a pair working on it alone.
+//
+// Used for launches of more problems than one resident wave holds.
+__global__ void __launch_bounds__(kThreads) erk_kernel_pool(const OdeArgs a) {
+    const int half = static_cast<int>(threadIdx.x & 1);
+    const unsigned pmask = 3u << (threadIdx.x & 30u);
+    const int leader = static_cast<int>(threadIdx.x & 31u & ~1u);
+    const bool up = half != 0;
+    const int64_t F = a.M * a.NP;
+    bool busy = false;
+    // the problem in hand
+    int64_t f = 0;                                  // result slot [m][p]
+    double fr[6];                                   // bg, lam, sigma, E, f_AA, f_DD
+    Slots sl;
+    const double *st = nullptr, *sv = nullptr, *yp = nullptr;
+    int ns = 0, si = 0, k = 0, status = PF_ST_OK;
+    double lnorm = 0.0, u = 0.0, t = 0.0, h = 1e-3, ll = 0.0;
+    uint32_t steps = 0;
+    bool fresh = true;                              // k1 must be evaluated
+    // yt: the full state at the stage points; after an accepted step it is the
+    // new state x, and x is read (k1 after an input switch, R at an
+    // observation time) only then, so x needs no copy of its own.
+    double yt[kNs];
+    double k1[kOwn], k2[kOwn], k3[kOwn], k4[kOwn], k5[kOwn], k6[kOwn], k7[kOwn], yo[kOwn];
+    double xo[kOwn];                                // the owner's components of x
+    for (;;) {
+        if (!busy) {
+            unsigned long long q = 0;
+            if (half == 0) q = atomicAdd(a.next, 1ull);
+            q = __shfl_sync(pmask, q, leader);
+            if (q >= static_cast<unsigned long long>(F)) break;
+            const int pi = static_cast<int>(q / static_cast<unsigned long long>(a.M));
+            const int p = a.porder[pi];
+            const int64_t m = static_cast<int64_t>(q) - static_cast<int64_t>(pi) * a.M;
+            f = m * a.NP + p;
+            double th[36];
+            bool ok = true;
+            for (int i = 0; i < 36; ++i) {
+                th[i] = a.thetas[m * 36 + i];
+                ok = ok && isfinite(th[i]) && th[i] > 0.0;
+            }
+            ok = ok && th[33] < 1.0;                // FRET efficiency E in (0, 1)
+            if (!ok) {
+                if (half == 0) {
+                    a.ll_f[f] = __longlong_as_double(0x7FF8000000000000ll);
+                    a.st_f[f] = PF_ST_INVALID_THETA;
+                    if (a.steps_f) a.steps_f[f] = 0;
+                }
+                continue;
+            }
+            const double y0[kNs] = {th[27], 0.0, 0.1, 0.0, 0.7, 0.0, 0.68, 0.0, 0.26, 0.0, th[28], 0.0,
+                                    th[29], th[29]};
+#pragma unroll
+            for (int c = 0; c < kNs; ++c) yt[c] = y0[c];
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c) xo[c] = up ? (c < 6 ? yt[8 + c] : 0.0) : yt[c];
+            make_slots(half, th, sl);
+#pragma unroll
+            for (int i = 0; i < 6; ++i) fr[i] = th[30 + i];
+            st = a.sw_t + a.sw_off[p];
+            ns = a.sw_off[p + 1] - a.sw_off[p];
+            sv = a.sw_v + a.sw_off[p];
+            yp = a.y + static_cast<int64_t>(p) * a.K;
+            lnorm = -log(fr[2]) - 0.91893853320467274178;   // -log sigma - log(2 pi)/2
+            si = 0;                                   // next switch index with st[si] > t
+            while (si < ns && st[si] <= 0.0) ++si;
+            u = 0.0;
+            for (int i = 0; i < ns && st[i] <= 0.0; ++i) u = sv[i];
+            t = 0.0;
+            h = 1e-3;
+            ll = 0.0;
+            steps = 0;
+            status = PF_ST_OK;
+            fresh = true;
+            k = 0;
+            busy = true;
+        }
+        const double tk = a.obs[k];
+        if (!(t < tk)) {                              // at observation time k
+            const double R = fret(yt, fr);           // yt = x after the last accepted step
+            const double z = (yp[k] - R) / fr[2];
+            ll += lnorm - 0.5 * z * z;
+            if (++k == a.K) {
+                if (half == 0) {
+                    a.ll_f[f] = ll;
+                    a.st_f[f] = PF_ST_OK;
+                    if (a.steps_f) a.steps_f[f] = steps;
+                }
+                busy = false;
+            }
+            continue;
+        }
+        // one Dormand-Prince step towards the next stop (input switch or observation)
+        const double tstop = (si < ns && st[si] < tk) ? st[si] : tk;
+        if (fresh) {
+            rhs_pair(up, sl, yt, u, k1);
+            fresh = false;
+        }
+        bool last = false;
+        double hh = h;
+        if (t + hh >= tstop) {
+            hh = tstop - t;
+            last = true;
+        }
+#pragma unroll
+        for (int c = 0; c < kOwn; ++c) yo[c] = xo[c] + hh * (A21 * k1[c]);
+        exchange(pmask, up, yo, yt);
+        rhs_pair(up, sl, yt, u, k2);
+#pragma unroll
+        for (int c = 0; c < kOwn; ++c)
+            yo[c] = xo[c] + hh * (A31 * k1[c] + A32 * k2[c]);
+        exchange(pmask, up, yo, yt);
+        rhs_pair(up, sl, yt, u, k3);
+#pragma unroll
+        for (int c = 0; c < kOwn; ++c)
+            yo[c] = xo[c] + hh * (A41 * k1[c] + A42 * k2[c] + A43 * k3[c]);
+        exchange(pmask, up, yo, yt);
+        rhs_pair(up, sl, yt, u, k4);
+#pragma unroll
+        for (int c = 0; c < kOwn; ++c)
+            yo[c] = xo[c] + hh * (A51 * k1[c] + A52 * k2[c] + A53 * k3[c] + A54 * k4[c]);
+        exchange(pmask, up, yo, yt);
+        rhs_pair(up, sl, yt, u, k5);
+#pragma unroll
+        for (int c = 0; c < kOwn; ++c)
+            yo[c] = xo[c] + hh * (A61 * k1[c] + A62 * k2[c] + A63 * k3[c] + A64 * k4[c] + A65 * k5[c]);
+        exchange(pmask, up, yo, yt);
+        rhs_pair(up, sl, yt, u, k6);
+#pragma unroll
+        for (int c = 0; c < kOwn; ++c)
+            yo[c] = xo[c] + hh * (B1 * k1[c] + B3 * k3[c] + B4 * k4[c] + B5 * k5[c] + B6 * k6[c]);
+        exchange(pmask, up, yo, yt);
+        rhs_pair(up, sl, yt, u, k7);
+        double err = 0.0;
+#pragma unroll
+        for (int c = 0; c < kOwn; ++c) {
+            const double ei = hh * (E1 * k1[c] + E3 * k3[c] + E4 * k4[c] + E5 * k5[c] + E6 * k6[c] +
+                                    E7 * k7[c]);
+            const double sc = a.atol + a.rtol * fmax(fabs(xo[c]), fabs(yo[c]));
+            const double r = ei / sc;
+            if (!up || c < 6) err += r * r;
+        }
+        err += __shfl_xor_sync(pmask, err, 1);       // both halves, commutative: identical sums
+        err = sqrt(err / kNs);
+        if (!isfinite(err)) {
+            status = PF_ST_NONFINITE;
+        } else if (++steps > static_cast<uint32_t>(a.max_steps)) {
+            status = PF_ST_BUDGET;
+        } else if (err <= 1.0) {                      // accept
+            t = last ? tstop : t + hh;
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c) xo[c] = yo[c];
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c) k1[c] = k7[c];   // first same as last
+            const double fac = err > 0.0 ? fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2))) : 5.0;
+            if (!last || hh * fac < h) h = hh * fac;
+            if (last && si < ns && st[si] == tstop) {   // the input switches here
+                while (si < ns && st[si] <= tstop) u = sv[si++];
+                fresh = true;
+            }
+        } else {                                      // reject: shrink and retry
+            h = hh * fmax(0.2, 0.9 * pow(err, -0.2));
+        }
+        if (status != PF_ST_OK) {
+            if (half == 0) {
+                a.ll_f[f] = -INFINITY;
+                a.st_f[f] = static_cast<uint8_t>(status);
+                if (a.steps_f) a.steps_f[f] = steps;
+            }
+            busy = false;
+        }
+    }
+}
+
+// One wave: every pair of threads solves one problem (g = t >> 1),
+// pattern-major (g = p * M + m) so that the lanes of a warp share an input
+// pattern; used when all problems are resident at once.  Both lanes of a pair take the
 // same decisions (the error norm is summed over both halves in either order,
 // which is commutative), so they stay converged; a row's result depends on
 // its own inputs only.
@@ -152,7 +342,7 @@ constexpr double E1 = 71.0 / 57600.0, E3 = -71.0 / 16695.0, E4 = 71.0 / 1920.0,
 // one wave and otherwise would not: a grid of fewer problems than the GPU
 // holds gains more from having all of them resident than the spills cost.
 template <int MinBlocks>
-__global__ void __launch_bounds__(kThreads, MinBlocks) erk_kernel(const OdeArgs a) {
+__global__ void __launch_bounds__(kThreads, MinBlocks) erk_kernel_wave(const OdeArgs a) {
     const int64_t tg = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t g = tg >> 1;
     const int half = static_cast<int>(tg & 1);
@@ -283,7 +473,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks) erk_kernel(const OdeArgs 
             }
         }
         if (status != PF_ST_OK) break;
-        const double R = fret(yt, th);          // yt = x after the last accepted step
+        const double R = fret(yt, th + 30);     // yt = x after the last accepted step
         const double z = (yp[k] - R) / sigma;
         ll += lnorm - 0.5 * z * z;
     }
@@ -371,14 +561,22 @@ extern "C" int pf_erk_loglik(const double *thetas, int64_t M, const double *swit
     const int64_t F = M * NP;
     pf::OdeArgs a{};
     a.M = M; a.NP = NP; a.K = K; a.rtol = rtol; a.atol = atol; a.max_steps = max_steps;
-    pf::OBuf b_sw, b_obs, b_th, b_y, b_ll, b_st, b_llf, b_stf, b_steps;
-    // switch tables and observation times: one small host-to-device copy
-    std::vector<unsigned char> tab(sizeof(double) * (2 * (size_t)nsw + K) + sizeof(int32_t) * (NP + 1));
+    pf::OBuf b_sw, b_obs, b_th, b_y, b_ll, b_st, b_llf, b_stf, b_steps, b_ctr;
+    // switch tables, observation times, offsets and the patterns' hand-out
+    // order (most switches first: their integrations take the most steps):
+    // one small host-to-device copy
+    std::vector<int32_t> porder(NP);
+    for (int p = 0; p < NP; ++p) porder[p] = p;
+    std::stable_sort(porder.begin(), porder.end(), [&](int x, int y) {
+        return switch_offsets[x + 1] - switch_offsets[x] > switch_offsets[y + 1] - switch_offsets[y];
+    });
+    std::vector<unsigned char> tab(sizeof(double) * (2 * (size_t)nsw + K) + sizeof(int32_t) * (2 * (size_t)NP + 1));
     double *tt = reinterpret_cast<double *>(tab.data());
     std::copy(switch_times, switch_times + nsw, tt);
     std::copy(switch_values, switch_values + nsw, tt + nsw);
     std::copy(obs_times, obs_times + K, tt + 2 * nsw);
     std::copy(switch_offsets, switch_offsets + NP + 1, reinterpret_cast<int32_t *>(tt + 2 * nsw + K));
+    std::copy(porder.begin(), porder.end(), reinterpret_cast<int32_t *>(tt + 2 * nsw + K) + NP + 1);
     ODE_CUDA(b_sw.alloc(tab.size(), s), "alloc tables");
     ODE_CUDA(cudaMemcpyAsync(b_sw.p, tab.data(), tab.size(), cudaMemcpyHostToDevice, s), "copy tables");
     const double *dt = static_cast<const double *>(b_sw.p);
@@ -386,6 +584,7 @@ extern "C" int pf_erk_loglik(const double *thetas, int64_t M, const double *swit
     a.sw_v = dt + nsw;
     a.obs = dt + 2 * nsw;
     a.sw_off = reinterpret_cast<const int32_t *>(dt + 2 * nsw + K);
+    a.porder = a.sw_off + NP + 1;
     double *d_ll = loglik;
     uint8_t *d_st = status;
     const size_t n_th = sizeof(double) * 36 * (size_t)M, n_y = sizeof(double) * (size_t)NP * K;
@@ -419,17 +618,28 @@ extern "C" int pf_erk_loglik(const double *thetas, int64_t M, const double *swit
         a.steps_f = static_cast<uint32_t *>(b_steps.p);
     }
     const int64_t nblk = (2 * F + pf::kThreads - 1) / pf::kThreads;
+    ODE_CUDA(b_ctr.alloc(sizeof(unsigned long long), s), "alloc work counter");
+    ODE_CUDA(cudaMemsetAsync(b_ctr.p, 0, sizeof(unsigned long long), s), "clear work counter");
+    a.next = static_cast<unsigned long long *>(b_ctr.p);
     int dev = 0, sms = 0, occ_plain = 0, occ_capped = 0;
     ODE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     ODE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
-    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_plain, pf::erk_kernel<0>, pf::kThreads, 0),
+    int occ_pool = 0;
+    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_plain, pf::erk_kernel_wave<0>, pf::kThreads, 0),
              "occupancy");
-    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_capped, pf::erk_kernel<6>, pf::kThreads, 0),
+    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_capped, pf::erk_kernel_wave<6>, pf::kThreads, 0),
              "occupancy");
-    if (nblk > (int64_t)occ_plain * sms && nblk <= (int64_t)occ_capped * sms)
-        pf::erk_kernel<6><<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
+    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pool, pf::erk_kernel_pool, pf::kThreads, 0),
+             "occupancy");
+    // Problems that fit one resident wave run one per pair (the register-capped
+    // instance when the plain one would need a second wave); more problems run
+    // on persistent pairs that take them from a work counter.
+    if (nblk <= (int64_t)occ_plain * sms)
+        pf::erk_kernel_wave<0><<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
+    else if (nblk <= (int64_t)occ_capped * sms)
+        pf::erk_kernel_wave<6><<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
     else
-        pf::erk_kernel<0><<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
+        pf::erk_kernel_pool<<<(unsigned)((int64_t)std::max(1, occ_pool) * sms), pf::kThreads, 0, s>>>(a);
     ODE_CUDA(cudaGetLastError(), "ode launch");
     pf::erk_reduce_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(a.ll_f, a.st_f, M, NP, d_ll, d_st);
     ODE_CUDA(cudaGetLastError(), "ode reduce launch");

@@ -128,3 +128,18 @@ def test_full_size_erk_sampled(pf):
     # 64 rows run on the uncapped one: the same rows give the same bits
     sub = pf.pf_erk_loglik(th[:64], w.patterns, w.obs_times, y)
     assert np.array_equal(sub["loglik"], g["loglik"][:64])
+
+
+def test_persistent_pairs_equal_one_wave(pf):
+    """More problems than one resident wave (16 384 rows x 6 patterns) run on
+    persistent lane pairs fed by a work counter; each problem's result is the
+    one the one-wave kernel gives for the same row, bit for bit."""
+    w = W.erk()
+    w.M = 16384
+    th = w.thetas()
+    y = w.observations()
+    big = pf.pf_erk_loglik(th, w.patterns, w.obs_times, y, diagnostics=True)
+    assert (big["status"] == 0).all()
+    small = pf.pf_erk_loglik(th[:4096], w.patterns, w.obs_times, y, diagnostics=True)
+    assert np.array_equal(big["loglik"][:4096], small["loglik"])
+    assert np.array_equal(big["steps"][:4096], small["steps"])
