@@ -70,13 +70,10 @@ ZIG_FLOPS = 1.0 + P_WEDGE * (7.0 + P_WEDGE_OPEN * FP64_FLOPS_EXP + 0.5) + P_TAIL
 
 
 # DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression
-# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum on the 152-theta
-# case of the kernel (611 072 + 0 bytes) scaled by the filters processed
-# (x 4096/152) was 16.47e6.  The kernel has changed since those counters were
-# taken (its shared header gained the cluster exchange slot, its weight and
-# set-up code moved into shared helpers), so no figure is reported until they
-# are taken again.
-FILTER_TRAFFIC_BYTES = None
+# workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of the current
+# kernel on its 152-theta case (655 616 + 0 bytes, one launch) scaled by the
+# filters processed (x 4096/152).
+FILTER_TRAFFIC_BYTES = 655_616 * 4096 / 152
 
 
 def flops_per_event(R: int) -> float:
@@ -391,6 +388,11 @@ def main() -> None:
                          "(telegraph, birth_death); ode: the deterministic Erk-model likelihood")
     ap.add_argument("--ode-theta", type=int, default=4096,
                     help="--mode ode: theta rows per launch (the Erk batch size)")
+    ap.add_argument("--hetero-requests", type=int, default=64)
+    ap.add_argument("--hetero-cascade-theta", type=int, default=4096,
+                    help="--mode hetero: largest theta count of a cascade request")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="--mode hetero: the default launch shape instead of the batch autotuner's")
     ap.add_argument("--serve-seconds", type=float, default=10.0)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--cluster", type=int, default=-1,
@@ -579,14 +581,19 @@ def run_pattern(a) -> None:
     """Batching / serving measurements (one JSON line each)."""
     from paper_1606_08281_gb300 import serving
     if a.mode == "hetero":
-        mix = W.hetero_mix()
-        res = serving.run_hetero(mix, repeats=2)
+        mix = W.hetero_mix(n_requests=a.hetero_requests, max_theta_cascade=a.hetero_cascade_theta)
+        res = serving.run_hetero(mix, repeats=1, tune=not a.no_tune)
         line = {"metric": "theta-likelihoods/s", "mode": "hetero-batch",
                 "value": res["batched_theta_per_s"], "unit": "theta-likelihoods/s",
                 "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": "heterogeneous mix: 48 requests over birth_death / "
-                                       "gene_expression / cascade, theta 1-4096 (cascade 1-64), "
-                                       "N 256-4096, K 10-100 (seed 4001)"},
+                "config": {"workload": f"heterogeneous mix: {a.hetero_requests} requests over "
+                                       "birth_death / gene_expression / cascade, theta 1-4096 "
+                                       f"(cascade 1-{a.hetero_cascade_theta}), N 256-4096, K 10-100 "
+                                       "(seed 4001), plus one Lac-Gfp request (32 rows x 4 "
+                                       "trajectories, N 200, K 29); requests that cannot fill the "
+                                       "GPU alone split over clusters in both arms",
+                           "launch_shape": "batch autotuner on a 1/8 sample" if not a.no_tune
+                           else "defaults"},
                 "plain_per_request": res["plain_theta_per_s"], **res}
     else:
         stream = W.serving_stream(rate_hz=a.serve_rate, duration_s=a.serve_seconds)

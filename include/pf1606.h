@@ -407,6 +407,34 @@ typedef struct pf_ctx pf_ctx;
 int pf_ctx_create(pf_ctx **ctx, size_t mem_budget_bytes, int32_t n_slots, int32_t max_particles);
 
 /*
+ * Launch shape of a context's persistent kernels, fixed when its graphs are
+ * captured (pf_ctx_create_config; zero fields take the defaults).  None of
+ * these changes a result except cluster_blocks for the requests that ask to be
+ * split (their log-likelihoods' last places depend on the cluster size, as with
+ * pf_options.cluster_blocks).
+ *   block_threads  threads per filter block for each reaction tier (R <= 4 with
+ *                  U <= 4, R <= 8, R <= 16, R <= 32): a multiple of 32 in
+ *                  32..128; 0 = 128.
+ *   cluster_blocks blocks of the thread-block clusters over which the filters
+ *                  of requests with pf_request.cluster_blocks > 1 are split:
+ *                  2..PF_MAX_CLUSTER_BLOCKS; 0 = 4.  A split filter's share of
+ *                  the particles on one block must fit its 96 KB arena.
+ *   grab           filters a block (or cluster) takes from its kernel group's
+ *                  work list at a time: 1..64; 0 = 1.
+ * The autotuner (autotune.tune_batch) chooses these on a sample of a request
+ * mix.
+ */
+typedef struct {
+    int32_t block_threads[4];
+    int32_t cluster_blocks;
+    int32_t grab;
+} pf_ctx_config;
+
+/* pf_ctx_create_config -- pf_ctx_create with a launch shape (NULL: defaults). */
+int pf_ctx_create_config(pf_ctx **ctx, size_t mem_budget_bytes, int32_t n_slots,
+                         int32_t max_particles, const pf_ctx_config *cfg);
+
+/*
  * pf_ctx_load_problem -- copy a problem to the device (Sec. "General Task":
  * network, x0, observation times, T observed trajectories y [T][K][P],
  * C [P][U], sigma [P]); host pointers, same rules as pf_loglik.  Writes its
@@ -431,7 +459,12 @@ int pf_ctx_load_problem_model(pf_ctx *ctx, const pf_network *net, int32_t d, con
  * PF_ST_REJECTED (as pf_options.early_reject); NaN = evaluate every row fully.
  * theta_id_base: row m's theta id in the random-number counter is
  * theta_id_base + m (< 2^32), so that a level set's batch split over several
- * requests gives the values of one request over the whole batch. */
+ * requests gives the values of one request over the whole batch.
+ * cluster_blocks: 0 or 1, one block per filter; otherwise it must equal the
+ * context's cluster size, and each filter of the request runs split over a
+ * thread-block cluster of that many blocks (for requests with few, heavy
+ * filters, whose single-block filters would be the batch's tail); the results
+ * equal pf_loglik's with the same pf_options.cluster_blocks. */
 typedef struct {
     int32_t problem_id;
     int32_t d;
@@ -445,6 +478,7 @@ typedef struct {
     double *loglik;        /* [M] out */
     uint8_t *status;       /* [M] out, may be NULL */
     uint32_t theta_id_base;
+    int32_t cluster_blocks;
 } pf_request;
 
 /*

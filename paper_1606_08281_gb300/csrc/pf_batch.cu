@@ -38,8 +38,11 @@ namespace {
 using namespace dev;
 
 constexpr int kTiers = 4;             // (R<=4,U<=4 in registers), R<=8, R<=16, R<=32
-constexpr int kGroups = 2 * kTiers;   // x {population in shared memory, in a global slab}
-constexpr int kBlock = 128;
+// x {population in shared memory, in a global slab, split over a thread-block cluster}
+constexpr int kKinds = 3;
+constexpr int kGroups = kKinds * kTiers;
+constexpr int kBlock = 128;           // largest block; each tier's size is the context's choice
+constexpr size_t kClusterArena = 96u << 10;   // a cluster block's share of a split filter (bytes)
 constexpr int kMaxSlots = 8;
 constexpr int kMaxProblems = 256;
 // Work-list item: request (20 bits) | theta row (32 bits) | trajectory (12 bits)
@@ -90,11 +93,23 @@ __global__ void init_bounds_kernel(const BatchHeader *hdr, const RequestDev *req
     }
 }
 
+// The next work-list index of a block: thread 0 takes `grab` consecutive
+// indices at a time from the group's counter (fewer atomics; a coarser grain
+// balances less well at the end).  Returns the index (>= count: no work left).
+__device__ __forceinline__ unsigned long long next_item(unsigned long long *counter, int grab,
+                                                        unsigned long long &base, int &left) {
+    if (left == 0) {
+        base = atomicAdd(counter, static_cast<unsigned long long>(grab));
+        left = grab;
+    }
+    return base + static_cast<unsigned long long>(grab - left--);
+}
+
 template <int RM, int UM, bool GLOBAL>
 __global__ void __launch_bounds__(kBlock, 4)
 batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *items, int group,
              unsigned long long *counters, unsigned char *slab, size_t slab_bytes, double *ll_f,
-             uint8_t *st_f, unsigned long long *ev_f, const ZigTab *zig) {
+             uint8_t *st_f, unsigned long long *ev_f, const ZigTab *zig, int grab) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ SharedHead sh;
     __shared__ RequestDev rq;
@@ -107,10 +122,12 @@ batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *ite
     const long long begin = hdr->group_begin[group];
     const unsigned long long count = static_cast<unsigned long long>(hdr->group_count[group]);
     unsigned char *arrays = GLOBAL ? slab + static_cast<size_t>(blockIdx.x) * slab_bytes : smem;
+    unsigned long long base = 0;
+    int left = 0;
     for (;;) {
         __syncthreads();
         if (threadIdx.x == 0) {
-            cur = atomicAdd(&counters[group], 1ull);
+            cur = next_item(&counters[group], grab, base, left);
             if (cur < count) {
                 item = items[begin + static_cast<long long>(cur)];
                 rq = reqs[item >> kItemReqShift];
@@ -153,6 +170,77 @@ batch_kernel(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *ite
     }
 }
 
+// Filters of requests that asked to be split: one filter at a time on the C
+// blocks of a thread-block cluster (run_filter_cluster), the cluster taking
+// filters from its group's work list.  Block 0 of the cluster takes the next
+// index and the others read it through distributed shared memory, so every
+// block of the cluster works on the same filter and leaves the loop together.
+template <int RM, int UM>
+__global__ void __launch_bounds__(kBlock, 2)
+batch_kernel_cluster(const BatchHeader *hdr, const RequestDev *reqs, const uint64_t *items,
+                     int group, unsigned long long *counters, double *ll_f, uint8_t *st_f,
+                     unsigned long long *ev_f, const ZigTab *zig, int grab) {
+    namespace cg = cooperative_groups;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ SharedHead sh;
+    __shared__ RequestDev rq;
+    __shared__ unsigned long long cur, taken;
+    __shared__ const ProblemDev *loaded;
+    cg::cluster_group cl = cg::this_cluster();
+    const bool lead = cl.block_rank() == 0;
+    load_zig_table(sh.zig, zig);
+    if (threadIdx.x == 0) sh.zig_g = zig;
+    if (threadIdx.x == 0) loaded = nullptr;
+    const long long begin = hdr->group_begin[group];
+    const unsigned long long count = static_cast<unsigned long long>(hdr->group_count[group]);
+    unsigned long long base = 0;
+    int left = 0;
+    for (;;) {
+        cl.sync();   // every block is done with the previous filter's exchange slots
+        if (lead && threadIdx.x == 0) taken = next_item(&counters[group], grab, base, left);
+        cl.sync();
+        if (threadIdx.x == 0) {
+            cur = *cl.map_shared_rank(&taken, 0);
+            if (cur < count) rq = reqs[items[begin + static_cast<long long>(cur)] >> kItemReqShift];
+        }
+        __syncthreads();
+        if (cur >= count) break;
+        const uint64_t item = items[begin + static_cast<long long>(cur)];
+        if (rq.prob != loaded) {
+            const uint32_t *src = reinterpret_cast<const uint32_t *>(&rq.prob->net);
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&sh.net);
+            for (int i = threadIdx.x; i < static_cast<int>(sizeof(NetTables) / 4); i += blockDim.x)
+                dst[i] = src[i];
+            __syncthreads();
+            if (threadIdx.x == 0) loaded = rq.prob;
+            __syncthreads();
+        }
+        const uint32_t row = static_cast<uint32_t>(item >> kItemRowShift);
+        const int traj = static_cast<int>(item & 0xFFF);
+        const int64_t f = rq.filter_base + static_cast<int64_t>(row) * rq.T + traj;
+        FilterJob job;
+        job.theta = rq.thetas + static_cast<int64_t>(row) * rq.d;
+        job.obs_times = rq.prob->obs_times;
+        job.y = rq.prob->y + static_cast<int64_t>(traj) * rq.prob->K * sh.net.P;
+        job.K = rq.K;
+        job.N = rq.N;
+        job.mrow = rq.id_base + row;
+        job.traj = traj;
+        job.seed = rq.seed;
+        job.budget = rq.budget;
+        job.ll_out = ll_f + f;
+        job.st_out = st_f + f;
+        job.ev_out = ev_f + f;
+        job.dg_out = nullptr;
+        job.fs_out = nullptr;
+        job.ph_out = nullptr;
+        job.acc = rq.acc ? rq.acc + row : nullptr;
+        job.reject_below = rq.reject_below;
+        job.slack = rq.slack;
+        run_filter_cluster<RM, UM>(job, sh, smem);
+    }
+}
+
 // Per theta row of every request: sum over trajectories, in order (Supp. I).
 __global__ void batch_reduce_kernel(const BatchHeader *hdr, const RequestDev *reqs,
                                     const double *ll_f, const uint8_t *st_f, double *out_ll,
@@ -187,18 +275,32 @@ __global__ void batch_reduce_kernel(const BatchHeader *hdr, const RequestDev *re
 // ---------------------------------------------------------------- groups
 using BatchKernel = void (*)(const BatchHeader *, const RequestDev *, const uint64_t *, int,
                              unsigned long long *, unsigned char *, size_t, double *, uint8_t *,
-                             unsigned long long *, const ZigTab *);
+                             unsigned long long *, const ZigTab *, int);
+using ClusterKernel = void (*)(const BatchHeader *, const RequestDev *, const uint64_t *, int,
+                               unsigned long long *, double *, uint8_t *, unsigned long long *,
+                               const ZigTab *, int);
 
+// group g = kKinds * tier + kind; kind 0: population in shared memory, 1: in a
+// global slab, 2: split over a cluster (cluster_kernel)
 BatchKernel group_kernel(int g) {
     switch (g) {
         case 0: return batch_kernel<4, 4, false>;
         case 1: return batch_kernel<4, 4, true>;
-        case 2: return batch_kernel<8, 0, false>;
-        case 3: return batch_kernel<8, 0, true>;
-        case 4: return batch_kernel<16, 0, false>;
-        case 5: return batch_kernel<16, 0, true>;
-        case 6: return batch_kernel<32, 0, false>;
+        case 3: return batch_kernel<8, 0, false>;
+        case 4: return batch_kernel<8, 0, true>;
+        case 6: return batch_kernel<16, 0, false>;
+        case 7: return batch_kernel<16, 0, true>;
+        case 9: return batch_kernel<32, 0, false>;
         default: return batch_kernel<32, 0, true>;
+    }
+}
+
+ClusterKernel cluster_kernel(int tier) {
+    switch (tier) {
+        case 0: return batch_kernel_cluster<4, 4>;
+        case 1: return batch_kernel_cluster<8, 0>;
+        case 2: return batch_kernel_cluster<16, 0>;
+        default: return batch_kernel_cluster<32, 0>;
     }
 }
 
@@ -275,6 +377,9 @@ struct pf_ctx {
     int device = 0;
     size_t budget = 0, used = 0;
     int n_slots = 0, max_particles = 0;
+    int block_threads[kTiers] = {kBlock, kBlock, kBlock, kBlock};   // per reaction tier
+    int cluster = 4;           // blocks of the clusters that split requests asking for it
+    int grab = 1;              // filters a block takes from a work list at a time
     int64_t cap_req = 0, cap_items = 0, cap_rows = 0, cap_theta = 0;
     size_t slab_bytes = 0;
     std::vector<ProblemHost> problems;
@@ -358,18 +463,43 @@ int init_slot(pf_ctx *ctx, int si) {
     int sms = 0;
     CTX_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device), "attr");
     for (int g = 0; g < kGroups; ++g) {
-        const bool global = g & 1;
-        const int tier = g >> 1;
-        BatchKernel k = group_kernel(g);
-        s.smem[g] = global ? 0 : shared_arena(tier);
-        CTX_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      static_cast<int>(std::max<size_t>(s.smem[g], 1))),
-                 "smem attribute");
-        int occ = 0;
-        CTX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kBlock, s.smem[g]), "occupancy");
-        occ = std::max(1, global ? 1 : occ);
-        s.grid[g] = sms * occ;
-        if (global) CTX_CUDA(cudaMalloc(&s.slab[g], ctx->slab_bytes * s.grid[g]), "global slab");
+        const int kind = g % kKinds, tier = g / kKinds;
+        const int B = ctx->block_threads[tier];
+        if (kind == 2) {       // split filters: clusters of ctx->cluster blocks
+            ClusterKernel ck = cluster_kernel(tier);
+            s.smem[g] = kClusterArena;
+            CTX_CUDA(cudaFuncSetAttribute(ck, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(s.smem[g])),
+                     "smem attribute");
+            CTX_CUDA(cudaFuncSetAttribute(ck, cudaFuncAttributeNonPortableClusterSizeAllowed, 1),
+                     "cluster attribute");
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(static_cast<unsigned>(ctx->cluster * sms));
+            cfg.blockDim = dim3(static_cast<unsigned>(B));
+            cfg.dynamicSmemBytes = s.smem[g];
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = static_cast<unsigned>(ctx->cluster);
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            CTX_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, ck, &cfg), "cluster occupancy");
+            s.grid[g] = std::max(1, nclusters) * ctx->cluster;
+        } else {
+            const bool global = kind == 1;
+            BatchKernel k = group_kernel(g);
+            s.smem[g] = global ? 0 : shared_arena(tier);
+            CTX_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          static_cast<int>(std::max<size_t>(s.smem[g], 1))),
+                     "smem attribute");
+            int occ = 0;
+            CTX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, B, s.smem[g]), "occupancy");
+            occ = std::max(1, global ? 1 : occ);
+            s.grid[g] = sms * occ;
+            if (global) CTX_CUDA(cudaMalloc(&s.slab[g], ctx->slab_bytes * s.grid[g]), "global slab");
+        }
         CTX_CUDA(cudaStreamCreateWithFlags(&s.side[g], cudaStreamNonBlocking), "stream");
         CTX_CUDA(cudaEventCreateWithFlags(&s.join[g], cudaEventDisableTiming), "event");
     }
@@ -381,11 +511,35 @@ int init_slot(pf_ctx *ctx, int si) {
     reset_kernel<<<1, 32, 0, s.stream>>>(s.counters);
     init_bounds_kernel<<<sms, 256, 0, s.stream>>>(s.hdr_d, s.req_d);
     cudaEventRecord(s.fork, s.stream);
+    cudaError_t le = cudaSuccess;
     for (int g = 0; g < kGroups; ++g) {
+        const int kind = g % kKinds, tier = g / kKinds;
+        const int B = ctx->block_threads[tier];
         cudaStreamWaitEvent(s.side[g], s.fork, 0);
-        group_kernel(g)<<<s.grid[g], kBlock, s.smem[g], s.side[g]>>>(
-            s.hdr_d, s.req_d, s.items_d, g, s.counters, s.slab[g], ctx->slab_bytes, s.ll_f, s.st_f,
-            s.ev_f, zig);
+        if (kind == 2) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(static_cast<unsigned>(s.grid[g]));
+            cfg.blockDim = dim3(static_cast<unsigned>(B));
+            cfg.dynamicSmemBytes = s.smem[g];
+            cfg.stream = s.side[g];
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = static_cast<unsigned>(ctx->cluster);
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            const cudaError_t e1 = cudaLaunchKernelEx(&cfg, cluster_kernel(tier), s.hdr_d,
+                                                      static_cast<const RequestDev *>(s.req_d),
+                                                      static_cast<const uint64_t *>(s.items_d), g,
+                                                      s.counters, s.ll_f, s.st_f, s.ev_f, zig,
+                                                      ctx->grab);
+            if (le == cudaSuccess) le = e1;
+        } else {
+            group_kernel(g)<<<s.grid[g], B, s.smem[g], s.side[g]>>>(
+                s.hdr_d, s.req_d, s.items_d, g, s.counters, s.slab[g], ctx->slab_bytes, s.ll_f,
+                s.st_f, s.ev_f, zig, ctx->grab);
+        }
         cudaEventRecord(s.join[g], s.side[g]);
         cudaStreamWaitEvent(s.stream, s.join[g], 0);
     }
@@ -393,6 +547,10 @@ int init_slot(pf_ctx *ctx, int si) {
                                                         s.out_ll_d, s.out_st_d);
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamEndCapture(s.stream, &graph);
+    if (e == cudaSuccess && le != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        e = le;
+    }
     if (e != cudaSuccess) return pf::cuda_fail(e, "end capture");
     e = cudaGraphInstantiate(&s.exec, graph, 0);
     cudaGraphDestroy(graph);
@@ -419,6 +577,18 @@ int check_request(pf_ctx *ctx, const pf_request &r, ReqState &st) {
     if (rc) return rc;
     if (population_bytes(r.n_particles, p.net.U) > ctx->slab_bytes)
         return fail(PF_EINVAL, "N=%d, U=%d exceeds the context's particle storage", r.n_particles, p.net.U);
+    if (r.cluster_blocks > 1) {
+        const int C = r.cluster_blocks, N = r.n_particles;
+        if (C != ctx->cluster)
+            return fail(PF_EINVAL, "cluster_blocks %d: this context splits filters over %d blocks", C, ctx->cluster);
+        if (N - (C - 1) * ((N + C - 1) / C) < 1)
+            return fail(PF_EINVAL, "n_particles %d leaves a block of the %d-block cluster empty", N, C);
+        if (cluster_smem_bytes(N, C, p.net.U, false) + 1024 > kClusterArena)
+            return fail(PF_EINVAL, "a %d-block cluster's share of N=%d, U=%d exceeds %zu bytes", C, N, p.net.U,
+                        kClusterArena);
+    } else if (r.cluster_blocks < 0) {
+        return fail(PF_EINVAL, "cluster_blocks must be >= 0");
+    }
     st.req = r;
     st.req.K_use = K;
     st.req.event_budget = budget;
@@ -489,7 +659,8 @@ int launch_batch(pf_ctx *ctx, int si, const std::vector<ReqState *> &batch) {
         const ProblemHost &p = ctx->problems[r.problem_id];
         const int tier = tier_of(p.net);
         const bool global = population_bytes(r.n_particles, p.net.U) > shared_arena(tier);
-        auto &list = lists[2 * tier + (global ? 1 : 0)];
+        const int kind = r.cluster_blocks > 1 ? 2 : (global ? 1 : 0);
+        auto &list = lists[kKinds * tier + kind];
         const uint64_t rq = static_cast<uint64_t>(oi) << kItemReqShift;
         for (int64_t m = 0; m < r.M; ++m)
             for (int t = 0; t < p.T; ++t)
@@ -602,8 +773,26 @@ void worker_loop(pf_ctx *ctx) {
 extern "C" {
 
 int pf_ctx_create(pf_ctx **out, size_t mem_budget_bytes, int32_t n_slots, int32_t max_particles) {
+    return pf_ctx_create_config(out, mem_budget_bytes, n_slots, max_particles, nullptr);
+}
+
+int pf_ctx_create_config(pf_ctx **out, size_t mem_budget_bytes, int32_t n_slots,
+                         int32_t max_particles, const pf_ctx_config *cfg) {
     pf::clear_error();
     if (!out) return fail(PF_EINVAL, "ctx is NULL");
+    pf_ctx_config c{};
+    if (cfg) c = *cfg;
+    for (int t = 0; t < kTiers; ++t) {
+        const int B = c.block_threads[t] ? c.block_threads[t] : kBlock;
+        if (B < 32 || B > kBlock || B % 32)
+            return fail(PF_EINVAL, "block_threads[%d] = %d must be a multiple of 32 in 32..%d", t, B, kBlock);
+        c.block_threads[t] = B;
+    }
+    if (c.cluster_blocks == 0) c.cluster_blocks = 4;
+    if (c.cluster_blocks < 2 || c.cluster_blocks > PF_MAX_CLUSTER_BLOCKS)
+        return fail(PF_EINVAL, "cluster_blocks %d outside 2..%d", c.cluster_blocks, PF_MAX_CLUSTER_BLOCKS);
+    if (c.grab == 0) c.grab = 1;
+    if (c.grab < 1 || c.grab > 64) return fail(PF_EINVAL, "grab %d outside 1..64", c.grab);
     if (n_slots == 0) n_slots = 3;
     if (n_slots < 1 || n_slots > kMaxSlots) return fail(PF_EINVAL, "n_slots %d outside 1..%d", n_slots, kMaxSlots);
     if (max_particles == 0) max_particles = 4096;
@@ -612,6 +801,9 @@ int pf_ctx_create(pf_ctx **out, size_t mem_budget_bytes, int32_t n_slots, int32_
     auto *ctx = new (std::nothrow) pf_ctx();
     if (!ctx) return fail(PF_ENOMEM, "host allocation");
     cudaGetDevice(&ctx->device);
+    for (int t = 0; t < kTiers; ++t) ctx->block_threads[t] = c.block_threads[t];
+    ctx->cluster = c.cluster_blocks;
+    ctx->grab = c.grab;
     ctx->budget = mem_budget_bytes ? mem_budget_bytes : (size_t(1) << 30);
     ctx->n_slots = n_slots;
     ctx->max_particles = max_particles;

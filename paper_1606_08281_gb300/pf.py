@@ -31,7 +31,8 @@ EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philo
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",
             "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit", "pf_poll", "pf_ctx_stats",
             "pf_ctx_destroy", "pf_exp_variates", "pf_div_check", "pf_ctx_load_problem_model",
-            "pf_fsp_loglik", "pf_erk_loglik", "pf_convert_check"]
+            "pf_fsp_loglik", "pf_erk_loglik", "pf_convert_check",
+            "pf_ctx_create_config"]
 
 
 class PfError(RuntimeError):
@@ -51,7 +52,13 @@ class pf_request(ct.Structure):
                 ("M", ct.c_int64), ("n_particles", ct.c_int32), ("K_use", ct.c_int32),
                 ("seed", ct.c_uint64), ("event_budget", ct.c_uint64),
                 ("loglik_threshold", ct.c_double), ("loglik", ct.c_void_p),
-                ("status", ct.c_void_p), ("theta_id_base", ct.c_uint32)]
+                ("status", ct.c_void_p), ("theta_id_base", ct.c_uint32),
+                ("cluster_blocks", ct.c_int32)]
+
+
+class pf_ctx_config(ct.Structure):
+    _fields_ = [("block_threads", ct.c_int32 * 4), ("cluster_blocks", ct.c_int32),
+                ("grab", ct.c_int32)]
 
 
 class pf_model(ct.Structure):
@@ -147,6 +154,8 @@ def load():
             lib.pf_loglik_noalloc.restype = ct.c_int
             V = ct.c_void_p
             lib.pf_ctx_create.argtypes = [ct.POINTER(V), ct.c_size_t, ct.c_int32, ct.c_int32]
+            lib.pf_ctx_create_config.argtypes = [ct.POINTER(V), ct.c_size_t, ct.c_int32, ct.c_int32,
+                                                 ct.POINTER(pf_ctx_config)]
             lib.pf_ctx_load_problem.argtypes = [V, ct.POINTER(pf_network), ct.c_int32, P, P,
                                                 ct.c_int32, P, ct.c_int32, ct.c_int32, P, P,
                                                 ct.POINTER(ct.c_int32)]
@@ -169,7 +178,8 @@ def load():
             lib.pf_ctx_stats.argtypes = [V, ct.POINTER(ct.c_int64), ct.POINTER(ct.c_int64),
                                          ct.POINTER(ct.c_int64)]
             lib.pf_ctx_destroy.argtypes = [V]
-            for name in ("pf_ctx_create", "pf_ctx_load_problem", "pf_ctx_run_batch", "pf_submit",
+            for name in ("pf_ctx_create", "pf_ctx_create_config", "pf_ctx_load_problem",
+                         "pf_ctx_run_batch", "pf_submit",
                          "pf_poll", "pf_ctx_stats", "pf_ctx_destroy"):
                 getattr(lib, name).restype = ct.c_int
             _lib = lib
@@ -554,6 +564,20 @@ def pf_ctx_create(mem_budget_bytes: int = 0, n_slots: int = 0, max_particles: in
     return h
 
 
+def pf_ctx_create_config(mem_budget_bytes: int = 0, n_slots: int = 0, max_particles: int = 0,
+                         block_threads=(0, 0, 0, 0), cluster_blocks: int = 0, grab: int = 0):
+    """pf_ctx_create with a launch shape (pf_ctx_config): threads per filter
+    block for each reaction tier, the cluster size of split requests, and the
+    filters a block takes from a work list at a time (0 = defaults)."""
+    lib = load()
+    h = ct.c_void_p()
+    cfg = pf_ctx_config((ct.c_int32 * 4)(*[int(b) for b in block_threads]), int(cluster_blocks),
+                        int(grab))
+    _check(lib.pf_ctx_create_config(ct.byref(h), int(mem_budget_bytes), int(n_slots),
+                                    int(max_particles), ct.byref(cfg)), "pf_ctx_create_config")
+    return h
+
+
 def pf_ctx_load_problem(ctx, net: dict, d: int, x0, obs_times, y, C, sigma,
                         model: dict | None = None) -> int:
     """Load a problem into a context; `model` as in pf_loglik (uses
@@ -597,7 +621,7 @@ class Request:
 
     def __init__(self, problem_id: int, thetas, n_particles: int, seed: int, K_use: int = 0,
                  event_budget: int = 0, loglik_threshold: float = float("nan"),
-                 theta_id_base: int = 0):
+                 theta_id_base: int = 0, cluster_blocks: int = 0):
         self.thetas = _host(thetas, np.float64)
         if self.thetas.ndim == 1:
             self.thetas = self.thetas[None, :]
@@ -607,7 +631,8 @@ class Request:
         self.s = pf_request(int(problem_id), int(d), _hptr(self.thetas), int(M),
                             int(n_particles), int(K_use), int(seed) & (2**64 - 1),
                             int(event_budget), float(loglik_threshold),
-                            _hptr(self.loglik), _hptr(self.status), int(theta_id_base))
+                            _hptr(self.loglik), _hptr(self.status), int(theta_id_base),
+                            int(cluster_blocks))
         self.id = None
         self.t_submit = self.t_done = None
 

@@ -25,16 +25,17 @@ def _load_problems(ctx, names):
     ids = {}
     for name in names:
         w = W.get(name)
-        ids[name] = pf.pf_ctx_load_problem(ctx, w.net, w.R, w.x0, w.obs_times, w.observations(),
-                                           w.C, w.sigma)
+        ids[name] = pf.pf_ctx_load_problem(ctx, w.net, len(w.prior_lo), w.x0, w.obs_times,
+                                           w.observations(), w.C, w.sigma, model=w.model)
     return ids
 
 
-def _plain(spec, w):
+def _plain(spec, w, cluster_blocks: int = 0):
     K = spec.K_use
     thr = spec.threshold if np.isfinite(spec.threshold) else None
     return pf.pf_loglik(w.net, spec.thetas, w.x0, w.obs_times[:K], w.observations()[:, :K, :],
-                        w.C, w.sigma, spec.n_particles, spec.seed, reject_below=thr)
+                        w.C, w.sigma, spec.n_particles, spec.seed, reject_below=thr,
+                        model=w.model, cluster_blocks=cluster_blocks)
 
 
 def calibrate_thresholds(stream, rows: int = 256) -> dict:
@@ -56,11 +57,37 @@ def calibrate_thresholds(stream, rows: int = 256) -> dict:
     return out
 
 
-def run_hetero(mix, n_slots: int = 3, repeats: int = 1) -> dict:
+def run_hetero(mix, n_slots: int = 3, repeats: int = 1, tune: bool = True,
+               tune_cache=None) -> dict:
+    """The mix as one batch of a context (persistent kernels, one graph replay)
+    against plain per-request pf_loglik launches.  Requests whose filters
+    cannot fill the GPU alone (autotune.split_rule) run split over thread-block
+    clusters in both arms, with the same cluster size; the context's launch
+    shape comes from the batch autotuner on a sample of the mix (tune=True)."""
+    from . import autotune
     names = sorted({s.problem for s in mix})
     wl = {n: W.get(n) for n in names}
     rows = sum(len(s.thetas) for s in mix)
-    ctx = pf.pf_ctx_create(0, n_slots, 4096)
+    split = [autotune.split_rule(len(s.thetas) * wl[s.problem].T) for s in mix]
+
+    def make(ctx, ids, frac, cluster):
+        out = []
+        for s, sp in zip(mix, split):
+            m = max(1, int(np.ceil(len(s.thetas) * frac)))
+            out.append(pf.Request(ids[s.problem], s.thetas[:m], s.n_particles, s.seed,
+                                  K_use=s.K_use, cluster_blocks=cluster if sp else 0))
+        return out
+
+    shapes = [(s.problem, 1 << int(np.ceil(np.log2(len(s.thetas)))), s.n_particles, s.K_use,
+               bool(sp)) for s, sp in zip(mix, split)]
+    if tune:
+        cfg = autotune.tune_batch(make, shapes, cache=tune_cache,
+                                  load_problems=lambda c: _load_problems(c, names))
+    else:
+        cfg = {"block_threads": [128] * 4, "cluster_blocks": 4, "grab": 1}
+    C = int(cfg["cluster_blocks"])
+    ctx = pf.pf_ctx_create_config(0, n_slots, 4096, block_threads=tuple(cfg["block_threads"]),
+                                  cluster_blocks=C, grab=int(cfg["grab"]))
     try:
         ids = _load_problems(ctx, names)
         # warm-up: one small request per problem
@@ -68,8 +95,7 @@ def run_hetero(mix, n_slots: int = 3, repeats: int = 1) -> dict:
                                   for n in names])
         batched = []
         for _ in range(repeats):
-            reqs = [pf.Request(ids[s.problem], s.thetas, s.n_particles, s.seed, K_use=s.K_use)
-                    for s in mix]
+            reqs = make(ctx, ids, 1.0, C)
             t0 = time.perf_counter()
             pf.pf_ctx_run_batch(ctx, reqs)
             batched.append(time.perf_counter() - t0)
@@ -78,11 +104,13 @@ def run_hetero(mix, n_slots: int = 3, repeats: int = 1) -> dict:
         pf.pf_ctx_destroy(ctx)
     _plain(mix[0], wl[mix[0].problem])  # warm-up
     t0 = time.perf_counter()
-    plain = [_plain(s, wl[s.problem]) for s in mix]
+    plain = [_plain(s, wl[s.problem], C if sp else 0) for s, sp in zip(mix, split)]
     t_plain = time.perf_counter() - t0
     same = all(np.array_equal(r.loglik, p["loglik"]) for r, p in zip(reqs, plain))
     tb = float(np.min(batched))
-    return {"requests": len(mix), "theta_rows": rows,
+    return {"requests": len(mix), "theta_rows": rows, "split_requests": int(sum(split)),
+            "launch_shape": {k: cfg[k] for k in ("block_threads", "cluster_blocks", "grab")},
+            "tuner_timings_s": cfg.get("timings_s"),
             "batched_s": tb, "plain_s": t_plain,
             "batched_theta_per_s": rows / tb, "plain_theta_per_s": rows / t_plain,
             "speedup": t_plain / tb, "identical_results": bool(same),

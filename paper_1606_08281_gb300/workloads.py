@@ -444,13 +444,16 @@ class RequestSpec:
     threshold: float = float("nan")
 
 
-def hetero_mix(seed: int = 4001, n_requests: int = 48, max_theta: int = 4096,
-               max_theta_cascade: int = 64) -> list[RequestSpec]:
-    """Heterogeneous batch: problems uniform over the three networks, theta
-    counts log-uniform integers in [1, max_theta] ([1, max_theta_cascade] for
-    the 10-species cascade, whose filters cost ~100x more), particle counts
-    uniform over {256, 512, 1024, 2048, 4096}, observation prefix K uniform in
-    [10, 100] capped at the problem's K."""
+def hetero_mix(seed: int = 4001, n_requests: int = 64, max_theta: int = 4096,
+               max_theta_cascade: int = 4096, lac_gfp_rows: int = 32) -> list[RequestSpec]:
+    """Heterogeneous batch (the batched-launch configuration): problems uniform
+    over the three networks, theta counts log-uniform integers in
+    [1, max_theta] ([1, max_theta_cascade] for the 10-species cascade),
+    particle counts uniform over {256, 512, 1024, 2048, 4096}, observation
+    prefix K uniform in [10, 100] capped at the problem's K; plus, when
+    lac_gfp_rows > 0, one Lac-Gfp request (the paper's large stochastic
+    example: the first lac_gfp_rows rows of its workload, all 4 trajectories,
+    N = 200, K = 29)."""
     rng = np.random.default_rng(seed)
     names = ["birth_death", "gene_expression", "cascade"]
     wl = {n: get(n) for n in names}
@@ -465,6 +468,9 @@ def hetero_mix(seed: int = 4001, n_requests: int = 48, max_theta: int = 4096,
         K = min(w.K, int(rng.integers(10, 101)))
         th = log_uniform(rng, w.prior_lo, w.prior_hi, M)
         out.append(RequestSpec(name, th, N, K, int(seed * 1000 + i)))
+    if lac_gfp_rows > 0:
+        w = lac_gfp()
+        out.append(RequestSpec("lac_gfp", w.thetas(lac_gfp_rows), w.N, w.K, int(seed * 1000 + n_requests)))
     return out
 
 

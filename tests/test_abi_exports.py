@@ -56,7 +56,7 @@ def test_binding_names_match_the_header():
 
 
 STRUCTS = ["pf_network", "pf_model", "pf_options", "pf_fsp_options", "pf_ode_options",
-           "pf_request"]
+           "pf_request", "pf_ctx_config"]
 
 
 def test_binding_structs_match_the_header_layout(tmp_path):

@@ -240,3 +240,54 @@ def test_early_rejection_decisions_against_the_oracle(pf, ctx, problems):
         assert (st[~below] == 0).all()
         np.testing.assert_allclose(ll[~below], o["loglik"][~below], rtol=1e-9, atol=0)
         assert np.isneginf(ll[below]).all()
+
+
+def test_launch_shape_and_cluster_split(pf):
+    """A context with its own launch shape (threads per block for each tier,
+    two filters per work-list grab, 4-block clusters): requests run one block
+    per filter equal their plain calls bit for bit whatever the shape; requests
+    asking to be split equal pf_loglik with the same cluster size and the
+    oracle; a Lac-Gfp request (model extensions) split in the mix too."""
+    from oracle import pf_oracle
+    c = pf.pf_ctx_create_config(0, 2, 4096, block_threads=(64, 96, 128, 96), cluster_blocks=4,
+                                grab=2)
+    try:
+        names = ("birth_death", "gene_expression", "cascade", "lac_gfp")
+        wl = {n: W.get(n) for n in names}
+        pids = {n: pf.pf_ctx_load_problem(c, wl[n].net, len(wl[n].prior_lo), wl[n].x0,
+                                          wl[n].obs_times, wl[n].observations(), wl[n].C,
+                                          wl[n].sigma, model=wl[n].model) for n in names}
+        specs = [("birth_death", 30, 100, 20, 71, 0), ("gene_expression", 5, 1000, 8, 72, 4),
+                 ("cascade", 2, 512, 4, 73, 4), ("lac_gfp", 3, 200, 4, 74, 4),
+                 ("gene_expression", 4, 600, 6, 75, 0)]
+        reqs = []
+        for name, M, N, K, seed, C in specs:
+            w = wl[name]
+            # Lac-Gfp: the workload's first rows (its prior's tail holds filters
+            # of 10^9 reactions, beyond the oracle in a test)
+            th = (w.thetas(M) if name == "lac_gfp" else
+                  W.log_uniform(np.random.default_rng(seed), w.prior_lo, w.prior_hi, M))
+            reqs.append((pf.Request(pids[name], th, N, seed, K_use=K, cluster_blocks=C), w, th, N,
+                         seed, K, C))
+        pf.pf_ctx_run_batch(c, [r[0] for r in reqs])
+        for r, w, th, N, seed, K, C in reqs:
+            ref = pf.pf_loglik(w.net, th, w.x0, w.obs_times[:K], w.observations()[:, :K, :], w.C,
+                               w.sigma, N, seed, model=w.model, cluster_blocks=C)
+            assert (r.status == ref["status"]).all(), w.name
+            assert np.array_equal(r.loglik, ref["loglik"]), (w.name, C)
+            o = pf_oracle.pf_loglik(w.net, th, w.x0, w.obs_times[:K], w.observations()[:, :K, :],
+                                    w.C, w.sigma, N, seed, model=w.model)
+            ok = o["status"] == 0
+            assert (r.status == o["status"]).all()
+            np.testing.assert_allclose(r.loglik[ok], o["loglik"][ok], rtol=1e-9, atol=0)
+        # a split request must use the context's cluster size
+        with pytest.raises(pf.PfError) as e:
+            pf.pf_submit(c, pf.Request(pids["gene_expression"], reqs[1][2], 600, 1, K_use=4,
+                                       cluster_blocks=2))
+        assert e.value.code == pf.PF_EINVAL
+    finally:
+        pf.pf_ctx_destroy(c)
+    with pytest.raises(pf.PfError):
+        pf.pf_ctx_create_config(0, 1, 1024, block_threads=(48, 0, 0, 0))
+    with pytest.raises(pf.PfError):
+        pf.pf_ctx_create_config(0, 1, 1024, cluster_blocks=9)
