@@ -418,12 +418,15 @@ int pf_ctx_create(pf_ctx **ctx, size_t mem_budget_bytes, int32_t n_slots, int32_
  *   cluster_blocks blocks of the thread-block clusters over which the filters
  *                  of requests with pf_request.cluster_blocks > 1 are split:
  *                  2..PF_MAX_CLUSTER_BLOCKS; 0 = 4.  A split filter's share of
- *                  the particles on one block must fit its 96 KB arena.
+ *                  the particles on one block, ceil(N/C) (12 + 8U) + 16 bytes,
+ *                  must fit PF_CTX_CLUSTER_ARENA less 1 KB (else PF_EINVAL at
+ *                  submission).
  *   grab           filters a block (or cluster) takes from its kernel group's
  *                  work list at a time: 1..64; 0 = 1.
  * The autotuner (autotune.tune_batch) chooses these on a sample of a request
  * mix.
  */
+#define PF_CTX_CLUSTER_ARENA (96u << 10)
 typedef struct {
     int32_t block_threads[4];
     int32_t cluster_blocks;
@@ -501,8 +504,10 @@ int pf_submit(pf_ctx *ctx, const pf_request *req, int64_t *req_id);
 /*
  * pf_poll -- PF_OK when request req_id has finished (its loglik/status arrays
  * are written; the id is then forgotten), PF_EAGAIN while it is queued or
- * running, PF_ENOTFOUND for an unknown id.  If wait_ms > 0 the call blocks up
- * to that long.  t_submit / t_done (may be NULL) receive the submission and
+ * running, PF_ENOTFOUND for an unknown id, PF_ECUDA when its batch failed on
+ * the device (the worker notices a failed batch through the slot's event
+ * within about 200 us; the CUDA context is then unusable, and every later
+ * batch fails the same way).  If wait_ms > 0 the call blocks up to that long.  t_submit / t_done (may be NULL) receive the submission and
  * completion times in seconds on the context's steady clock.
  */
 int pf_poll(pf_ctx *ctx, int64_t req_id, int32_t wait_ms, double *t_submit, double *t_done);

@@ -42,7 +42,7 @@ constexpr int kTiers = 4;             // (R<=4,U<=4 in registers), R<=8, R<=16, 
 constexpr int kKinds = 3;
 constexpr int kGroups = kKinds * kTiers;
 constexpr int kBlock = 128;           // largest block; each tier's size is the context's choice
-constexpr size_t kClusterArena = 96u << 10;   // a cluster block's share of a split filter (bytes)
+constexpr size_t kClusterArena = PF_CTX_CLUSTER_ARENA;   // a cluster block's share of a split filter
 constexpr int kMaxSlots = 8;
 constexpr int kMaxProblems = 256;
 // Work-list item: request (20 bits) | theta row (32 bits) | trajectory (12 bits)
@@ -204,7 +204,12 @@ batch_kernel_cluster(const BatchHeader *hdr, const RequestDev *reqs, const uint6
             if (cur < count) rq = reqs[items[begin + static_cast<long long>(cur)] >> kItemReqShift];
         }
         __syncthreads();
-        if (cur >= count) break;
+        if (cur >= count) {
+            // block 0 may leave only once every block has read its `taken`
+            // (no block reads the shared memory of a block that has exited)
+            cl.sync();
+            break;
+        }
         const uint64_t item = items[begin + static_cast<long long>(cur)];
         if (rq.prob != loaded) {
             const uint32_t *src = reinterpret_cast<const uint32_t *>(&rq.prob->net);
@@ -719,9 +724,19 @@ void worker_loop(pf_ctx *ctx) {
         // reap finished slots
         for (int si = 0; si < ctx->n_slots; ++si) {
             Slot &s = ctx->slots[si];
-            if (s.busy && s.finished.load()) {
+            if (!s.busy) continue;
+            if (s.finished.load()) {
                 cudaError_t e = cudaEventSynchronize(s.done);
                 finish_slot(ctx, si, e == cudaSuccess ? PF_OK : PF_ECUDA);
+                ctx->cv.notify_all();
+                continue;
+            }
+            // A host function queued behind a failed launch is never called:
+            // a device error reaches the requests through the slot's event.
+            const cudaError_t q = cudaEventQuery(s.done);
+            if (q != cudaSuccess && q != cudaErrorNotReady) {
+                ctx->worker_error = PF_ECUDA;
+                finish_slot(ctx, si, PF_ECUDA);
                 ctx->cv.notify_all();
             }
         }

@@ -26,6 +26,17 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT, PF_EAGAIN, PF_ENOTFOUND, PF_
 PF_ST_OK, PF_ST_BUDGET, PF_ST_NONFINITE, PF_ST_INVALID_THETA, PF_ST_REJECTED = 0, 1, 2, 3, 4
 PF_SCHED_AUTO, PF_SCHED_NATURAL, PF_SCHED_HEAVY_FIRST = 0, 1, 2
 PF_MAX_CLUSTER_BLOCKS = 8
+PF_CTX_CLUSTER_ARENA = 96 << 10
+
+
+def split_fits(n_particles: int, cluster_blocks: int, n_species: int) -> bool:
+    """Whether a batch request of N particles of U species can run split over
+    a cluster of C blocks (pf_ctx_config.cluster_blocks in include/pf1606.h):
+    every block holds a particle and its share, ceil(N/C) (12 + 8U) + 16
+    bytes, fits PF_CTX_CLUSTER_ARENA less 1 KB."""
+    C, N = int(cluster_blocks), int(n_particles)
+    np_ = -(-N // C)
+    return N - (C - 1) * np_ >= 1 and np_ * (12 + 8 * int(n_species)) + 16 + 1024 <= PF_CTX_CLUSTER_ARENA
 
 EXPORTED = ["pf_loglik", "pf_strerror", "pf_last_error", "pf_version", "pf_philox4x32_10",
             "pf_fp64_probe", "pf_neg_log_u53", "pf_loglik_noalloc", "pf_ctx_create",

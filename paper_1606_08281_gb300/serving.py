@@ -70,9 +70,14 @@ def run_hetero(mix, n_slots: int = 3, repeats: int = 1, tune: bool = True,
     rows = sum(len(s.thetas) for s in mix)
     split = [autotune.split_rule(len(s.thetas) * wl[s.problem].T) for s in mix]
 
+    def splits(cluster):
+        # a request splits when it cannot fill the GPU and its share fits a cluster block
+        return [sp and pf.split_fits(s.n_particles, cluster, wl[s.problem].U)
+                for s, sp in zip(mix, split)]
+
     def make(ctx, ids, frac, cluster):
         out = []
-        for s, sp in zip(mix, split):
+        for s, sp in zip(mix, splits(cluster)):
             m = max(1, int(np.ceil(len(s.thetas) * frac)))
             out.append(pf.Request(ids[s.problem], s.thetas[:m], s.n_particles, s.seed,
                                   K_use=s.K_use, cluster_blocks=cluster if sp else 0))
@@ -86,6 +91,7 @@ def run_hetero(mix, n_slots: int = 3, repeats: int = 1, tune: bool = True,
     else:
         cfg = {"block_threads": [128] * 4, "cluster_blocks": 4, "grab": 1}
     C = int(cfg["cluster_blocks"])
+    split = splits(C)
     ctx = pf.pf_ctx_create_config(0, n_slots, 4096, block_threads=tuple(cfg["block_threads"]),
                                   cluster_blocks=C, grab=int(cfg["grab"]))
     try:
@@ -135,24 +141,28 @@ def serve_batched(stream, n_slots: int = 3, mem_budget: int = 0) -> dict:
         reqs = [pf.Request(ids[s.problem], s.thetas, s.n_particles, s.seed, K_use=s.K_use,
                            loglik_threshold=s.threshold) for s in stream]
         submit_clock = {}
-        done = threading.Event()
+        failed = []
 
         def submitter():
             t0 = time.perf_counter()
-            for r, s in zip(reqs, stream):
-                dt = s.arrival_s - (time.perf_counter() - t0)
-                if dt > 0:
-                    time.sleep(dt)
-                pf.pf_submit(ctx, r)
-                submit_clock[r.id] = time.perf_counter()
-            done.set()
+            try:
+                for r, s in zip(reqs, stream):
+                    dt = s.arrival_s - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(dt)
+                    pf.pf_submit(ctx, r)
+                    submit_clock[r.id] = time.perf_counter()
+            except Exception as e:  # surfaced by the polling loop below
+                failed.append(e)
 
-        th = threading.Thread(target=submitter)
+        th = threading.Thread(target=submitter, daemon=True)
         th.start()
         lat = []
         finish = []
         for r in reqs:
             while r.id is None:
+                if failed:
+                    raise failed[0]
                 time.sleep(0.0005)
             while not pf.pf_poll(ctx, r, wait_ms=50):
                 pass

@@ -291,3 +291,37 @@ def test_launch_shape_and_cluster_split(pf):
         pf.pf_ctx_create_config(0, 1, 1024, block_threads=(48, 0, 0, 0))
     with pytest.raises(pf.PfError):
         pf.pf_ctx_create_config(0, 1, 1024, cluster_blocks=9)
+
+
+def test_many_batches_through_the_cluster_groups(pf):
+    """Hundreds of graph replays of one context whose graph carries the
+    cluster groups of every tier (most of them empty in a batch): every batch
+    finishes, and a split request and a one-block request give the same bits
+    in every replay.  Guards the cluster groups' exit (no block leaves while
+    another still reads its shared memory) and the worker's completion path."""
+    c = pf.pf_ctx_create_config(0, 3, 1024, cluster_blocks=4, grab=2)
+    try:
+        w = W.get("birth_death")
+        pid = pf.pf_ctx_load_problem(c, w.net, len(w.prior_lo), w.x0, w.obs_times,
+                                     w.observations(), w.C, w.sigma)
+        th = W.log_uniform(np.random.default_rng(91), w.prior_lo, w.prior_hi, 3)
+        first = None
+        for i in range(400):
+            reqs = [pf.Request(pid, th, 100, 5, K_use=6, cluster_blocks=4),
+                    pf.Request(pid, th, 100, 5, K_use=6)]
+            if i % 2:                        # the same requests by pf_submit / pf_poll
+                for r in reqs:
+                    pf.pf_submit(c, r)
+                for r in reqs:
+                    while not pf.pf_poll(c, r, wait_ms=1000):
+                        pass
+            else:
+                pf.pf_ctx_run_batch(c, reqs)
+            got = [r.loglik.copy() for r in reqs]
+            if first is None:
+                first = got
+            for a, b in zip(got, first):
+                assert np.array_equal(a, b), i
+        assert pf.pf_ctx_stats(c)["batches"] >= 400
+    finally:
+        pf.pf_ctx_destroy(c)
