@@ -592,7 +592,7 @@ def run_pattern(a) -> None:
                                        "(seed 4001), plus one Lac-Gfp request (32 rows x 4 "
                                        "trajectories, N 200, K 29); requests that cannot fill the "
                                        "GPU alone split over clusters in both arms",
-                           "launch_shape": "batch autotuner on a 1/8 sample" if not a.no_tune
+                           "launch_shape": "batch autotuner on a 1/32 sample" if not a.no_tune
                            else "defaults"},
                 "plain_per_request": res["plain_theta_per_s"], **res}
     else:

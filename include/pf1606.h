@@ -401,8 +401,12 @@ typedef struct pf_ctx pf_ctx;
  *   n_slots           batches that may be in flight at once (1..8; 0 = 3):
  *                     each slot owns its tables, stream and captured graph.
  *   max_particles     largest N a request may use (0 = 4096).
- * Allocates all slot memory up front.  Returns PF_OK, PF_EINVAL, PF_ENOMEM or
- * PF_ECUDA.
+ * Allocates all slot memory up front.  A filter's population N (12 + 4U) + 16
+ * bytes runs in a shared-memory arena sized for 4 blocks per SM if it fits,
+ * else in one sized for 2 blocks per SM, else in a global-memory slab (2
+ * blocks per SM, as pf_loglik); the arenas are what the occupancy calculator
+ * gives for the tier's kernel and block size.  Returns PF_OK, PF_EINVAL,
+ * PF_ENOMEM or PF_ECUDA.
  */
 int pf_ctx_create(pf_ctx **ctx, size_t mem_budget_bytes, int32_t n_slots, int32_t max_particles);
 

@@ -38,8 +38,9 @@ namespace {
 using namespace dev;
 
 constexpr int kTiers = 4;             // (R<=4,U<=4 in registers), R<=8, R<=16, R<=32
-// x {population in shared memory, in a global slab, split over a thread-block cluster}
-constexpr int kKinds = 3;
+// x {population in a shared-memory arena sized for 4 blocks per SM, in a global
+//    slab, split over a thread-block cluster, in an arena sized for 2 blocks per SM}
+constexpr int kKinds = 4;
 constexpr int kGroups = kKinds * kTiers;
 constexpr int kBlock = 128;           // largest block; each tier's size is the context's choice
 constexpr size_t kClusterArena = PF_CTX_CLUSTER_ARENA;   // a cluster block's share of a split filter
@@ -285,18 +286,15 @@ using ClusterKernel = void (*)(const BatchHeader *, const RequestDev *, const ui
                                unsigned long long *, double *, uint8_t *, unsigned long long *,
                                const ZigTab *, int);
 
-// group g = kKinds * tier + kind; kind 0: population in shared memory, 1: in a
-// global slab, 2: split over a cluster (cluster_kernel)
-BatchKernel group_kernel(int g) {
-    switch (g) {
-        case 0: return batch_kernel<4, 4, false>;
-        case 1: return batch_kernel<4, 4, true>;
-        case 3: return batch_kernel<8, 0, false>;
-        case 4: return batch_kernel<8, 0, true>;
-        case 6: return batch_kernel<16, 0, false>;
-        case 7: return batch_kernel<16, 0, true>;
-        case 9: return batch_kernel<32, 0, false>;
-        default: return batch_kernel<32, 0, true>;
+// group g = kKinds * tier + kind; kind 0: population in the small shared-memory
+// arena, 1: in a global slab, 2: split over a cluster (cluster_kernel), 3: in
+// the large arena.  Kinds 0 and 3 run the same kernel with different arenas.
+BatchKernel group_kernel(int tier, bool global) {
+    switch (tier) {
+        case 0: return global ? batch_kernel<4, 4, true> : batch_kernel<4, 4, false>;
+        case 1: return global ? batch_kernel<8, 0, true> : batch_kernel<8, 0, false>;
+        case 2: return global ? batch_kernel<16, 0, true> : batch_kernel<16, 0, false>;
+        default: return global ? batch_kernel<32, 0, true> : batch_kernel<32, 0, false>;
     }
 }
 
@@ -316,11 +314,12 @@ int tier_of(const NetTables &t) {
     return 3;
 }
 
-// Shared-memory population arena of the on-chip groups (bytes), next to the
-// ~32 KB of per-block tables: tier 0 fits four blocks per SM (up to ~1200
-// particles of 2 species), the larger tiers three (e.g. 700 particles of 10
-// species).
-size_t shared_arena(int tier) { return tier == 0 ? 24u << 10 : 36u << 10; }
+// Blocks per SM of the two on-chip kinds: the small arena keeps the filter
+// kernels' own occupancy (4 blocks of 128 threads: e.g. 512 particles of 10
+// species, 1300 of 2), the large one takes populations up to about 80 KB at 2
+// blocks per SM (e.g. 4096 particles of 2 species, 1500 of 10), as a plain
+// pf_loglik launch sized for them would.  Larger populations go to the slabs.
+constexpr int kSmallArenaBlocks = 4, kLargeArenaBlocks = 2;
 
 size_t population_bytes(int N, int U) { return filter_smem_bytes(N, U, false); }
 
@@ -387,6 +386,7 @@ struct pf_ctx {
     int grab = 1;              // filters a block takes from a work list at a time
     int64_t cap_req = 0, cap_items = 0, cap_rows = 0, cap_theta = 0;
     size_t slab_bytes = 0;
+    size_t arena[kTiers][2] = {};   // population bytes of the small and the large arena
     std::vector<ProblemHost> problems;
     Slot slots[kMaxSlots];
     std::mutex mu;
@@ -448,6 +448,27 @@ cudaError_t mapped(T **h, T **d, size_t n) {
         if (e_ != cudaSuccess) return pf::cuda_fail(e_, what);        \
     } while (0)
 
+// The two on-chip arenas of each tier: the dynamic shared memory a block can
+// have with kSmallArenaBlocks / kLargeArenaBlocks blocks per SM (16-byte
+// multiples), for the context's block size.
+int size_arenas(pf_ctx *ctx) {
+    for (int t = 0; t < kTiers; ++t) {
+        const void *k = reinterpret_cast<const void *>(group_kernel(t, false));
+        const cudaError_t e = static_cast<cudaError_t>(pf::raise_smem_limit(k));
+        if (e != cudaSuccess) return pf::cuda_fail(e, "smem attribute");
+        size_t small = 0, large = 0;
+        CTX_CUDA(cudaOccupancyAvailableDynamicSMemPerBlock(&small, group_kernel(t, false), kSmallArenaBlocks,
+                                                           ctx->block_threads[t]),
+                 "arena size");
+        CTX_CUDA(cudaOccupancyAvailableDynamicSMemPerBlock(&large, group_kernel(t, false), kLargeArenaBlocks,
+                                                           ctx->block_threads[t]),
+                 "arena size");
+        ctx->arena[t][0] = small & ~size_t(15);
+        ctx->arena[t][1] = std::max(small, large) & ~size_t(15);
+    }
+    return PF_OK;
+}
+
 int init_slot(pf_ctx *ctx, int si) {
     Slot &s = ctx->slots[si];
     CTX_CUDA(cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking), "stream");
@@ -494,15 +515,14 @@ int init_slot(pf_ctx *ctx, int si) {
             s.grid[g] = std::max(1, nclusters) * ctx->cluster;
         } else {
             const bool global = kind == 1;
-            BatchKernel k = group_kernel(g);
-            s.smem[g] = global ? 0 : shared_arena(tier);
-            CTX_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          static_cast<int>(std::max<size_t>(s.smem[g], 1))),
-                     "smem attribute");
+            BatchKernel k = group_kernel(tier, global);
+            s.smem[g] = global ? 0 : ctx->arena[tier][kind == 3 ? 1 : 0];
             int occ = 0;
             CTX_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, B, s.smem[g]), "occupancy");
-            occ = std::max(1, global ? 1 : occ);
-            s.grid[g] = sms * occ;
+            occ = std::max(1, occ);
+            // slabs: as many blocks as a plain pf_loglik launch uses (their
+            // populations stay in L2)
+            s.grid[g] = global ? std::min(pf::global_grid(sms), sms * occ) : sms * occ;
             if (global) CTX_CUDA(cudaMalloc(&s.slab[g], ctx->slab_bytes * s.grid[g]), "global slab");
         }
         CTX_CUDA(cudaStreamCreateWithFlags(&s.side[g], cudaStreamNonBlocking), "stream");
@@ -541,7 +561,7 @@ int init_slot(pf_ctx *ctx, int si) {
                                                       ctx->grab);
             if (le == cudaSuccess) le = e1;
         } else {
-            group_kernel(g)<<<s.grid[g], B, s.smem[g], s.side[g]>>>(
+            group_kernel(tier, kind == 1)<<<s.grid[g], B, s.smem[g], s.side[g]>>>(
                 s.hdr_d, s.req_d, s.items_d, g, s.counters, s.slab[g], ctx->slab_bytes, s.ll_f,
                 s.st_f, s.ev_f, zig, ctx->grab);
         }
@@ -663,8 +683,10 @@ int launch_batch(pf_ctx *ctx, int si, const std::vector<ReqState *> &batch) {
         const pf_request &r = st->req;
         const ProblemHost &p = ctx->problems[r.problem_id];
         const int tier = tier_of(p.net);
-        const bool global = population_bytes(r.n_particles, p.net.U) > shared_arena(tier);
-        const int kind = r.cluster_blocks > 1 ? 2 : (global ? 1 : 0);
+        const size_t pop = population_bytes(r.n_particles, p.net.U);
+        const int kind = r.cluster_blocks > 1 ? 2
+                         : pop <= ctx->arena[tier][0] ? 0
+                         : pop <= ctx->arena[tier][1] ? 3 : 1;
         auto &list = lists[kKinds * tier + kind];
         const uint64_t rq = static_cast<uint64_t>(oi) << kItemReqShift;
         for (int64_t m = 0; m < r.M; ++m)
@@ -828,6 +850,10 @@ int pf_ctx_create_config(pf_ctx **out, size_t mem_budget_bytes, int32_t n_slots,
     ctx->cap_theta = int64_t(1) << 23;
     ctx->slab_bytes = population_bytes(max_particles, PF_MAX_SPECIES);
     ctx->problems.reserve(kMaxProblems);
+    if (const int rc = size_arenas(ctx); rc != PF_OK) {
+        delete ctx;
+        return rc;
+    }
     for (int si = 0; si < n_slots; ++si) {
         const int rc = init_slot(ctx, si);
         if (rc != PF_OK) {

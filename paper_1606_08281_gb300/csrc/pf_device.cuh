@@ -364,7 +364,7 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N,
                 // the reaction, chosen before the time test so that both
                 // chains overlap (it is used only if the event is in time)
                 const uint64_t v2 = r1 >> 11;                  // u2 = v2 2^-53 in [0, 1)
-                const double target = __dmul_rn(v2 ? scaled_u53(v2) : 0.0, a0);
+                const double target = __dmul_rn(scaled_u53_or_zero(v2), a0);
                 const long long tb = dbits(target);
                 int chosen = 0;                                // first r with target < S_r
                 if constexpr (kDepList) {

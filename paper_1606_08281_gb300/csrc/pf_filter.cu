@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(128) pilot_kernel(const FilterArgs args, uint3
         const uint64_t v2 = ((static_cast<uint64_t>(w.w3) << 32) | w.w2) >> 11;
         t = __dadd_rn(t, __ddiv_rn(neg_log_u53((r0 >> 11) + 1ull, logt), run));
         if (__double_as_longlong(t) > t_end_bits) break;
-        const long long tb = __double_as_longlong(__dmul_rn(v2 ? scaled_u53(v2) : 0.0, run));
+        const long long tb = __double_as_longlong(__dmul_rn(scaled_u53_or_zero(v2), run));
         int chosen = 0;
 #pragma unroll
         for (int r = 0; r < RM; ++r) chosen += (r < R && __double_as_longlong(S[r]) <= tb) ? 1 : 0;

@@ -144,27 +144,60 @@ constexpr double B1 = 35.0 / 384.0, B3 = 500.0 / 1113.0, B4 = 125.0 / 192.0,
 constexpr double E1 = 71.0 / 57600.0, E3 = -71.0 / 16695.0, E4 = 71.0 / 1920.0,
                  E5 = -17253.0 / 339200.0, E6 = 22.0 / 525.0, E7 = -1.0 / 40.0;
 
-// Threads come in pairs; each pair takes problems (theta row m, input
-// pattern p) from a work counter, pattern by pattern (the patterns with the
-// most input switches, the costliest, first) and, within a pattern, rows in
-// order, so that the pairs of a warp mostly share a pattern and its stop
-// times.  The loop is flat: every trip is one unit of work of every pair -- a
-// new problem's set-up, one Dormand-Prince step, or the log-density at an
-// observation time -- so a pair that finishes its problem takes the next one
-// at once instead of idling until its warp-mates finish theirs, and the last
-// wave has no long tail.  Both lanes of a pair take the same decisions (the
-// error norm is summed over both halves in either order, which is
-// commutative), so they stay converged, and a problem's result depends on its
-// own inputs only: the step sequence is that of a pair working on it alone.
+// A problem in flight, as erk_kernel_pack moves it from one pair of lanes of
+// its block to another: each half's own components of x and of the first
+// stage (k1, valid unless fresh), and the step controller's scalars.  What
+// else a pair holds is a function of (theta row, pattern) and is rebuilt.
+struct Parked {
+    double xo[2][kOwn];
+    double k1[2][kOwn];
+    double t, h, ll, u;
+    int64_t f;
+    int32_t k, si, steps, fresh;
+};
+constexpr int kPackThreads = 256;                 // one block per SM: 128 pairs
+constexpr int kPackPairs = kPackThreads / 2;
+constexpr int kPackWarps = kPackThreads / 32;
+constexpr int kEpoch = 64;                        // trips between the block's barriers
+
+// Persistent lane pairs, one block of 128 pairs per SM.  Each pair takes
+// problems (theta row m, input pattern p) from a work counter, pattern by
+// pattern (the patterns with the most input switches, the costliest, first)
+// and, within a pattern, rows in order, so that the pairs of a warp mostly
+// share a pattern and its stop times.  The loop is flat: every trip is one
+// unit of work of a pair -- a new problem's set-up, one Dormand-Prince step,
+// or the log-density at an observation time -- so a pair that finishes its
+// problem takes the next one at once instead of idling until its warp-mates
+// finish theirs.  Both lanes of a pair take the same decisions (the error norm
+// is summed over both halves in either order, which is commutative), so they
+// stay converged, and a problem's result depends on its own inputs only: the
+// step sequence is that of a pair working on it alone.
 //
-// Used for launches of more problems than one resident wave holds.
-__global__ void __launch_bounds__(kThreads) erk_kernel_pool(const OdeArgs a) {
-    const int half = static_cast<int>(threadIdx.x & 1);
-    const unsigned pmask = 3u << (threadIdx.x & 30u);
-    const int leader = static_cast<int>(threadIdx.x & 31u & ~1u);
+// At the end of the launch, once the work counter is exhausted, the pairs that
+// still hold a problem become fewer and scattered over the block's warps, and
+// a warp pays the same FP64 issue for one busy pair as for sixteen.  So every
+// kEpoch trips the block meets at a barrier and, when the busy problems would
+// fit in fewer warps than they occupy, moves them to the block's lowest pairs
+// (through shared memory), leaving whole warps idle.  A move changes no
+// arithmetic: the problem continues from the same state, so its result is the
+// same bit for bit as on one pair from start to end.
+//
+// Used for launches of more problems than one resident wave of erk_kernel_wave
+// holds.
+__global__ void __launch_bounds__(kPackThreads, 1) erk_kernel_pack(const OdeArgs a) {
+    __shared__ Parked park[kPackPairs];
+    __shared__ int warp_busy[kPackWarps];
+    __shared__ int drained_s;
+    const int lane = static_cast<int>(threadIdx.x & 31u), warp = static_cast<int>(threadIdx.x >> 5);
+    const int half = lane & 1;
+    const unsigned pmask = 3u << (lane & 30);
+    const int leader = lane & 30;
     const bool up = half != 0;
+    const int pair = static_cast<int>(threadIdx.x >> 1);
     const int64_t F = a.M * a.NP;
-    bool busy = false;
+    if (threadIdx.x == 0) drained_s = 0;
+    __syncthreads();
+    bool busy = false, drained = false;
     // the problem in hand
     int64_t f = 0;                                  // result slot [m][p]
     double fr[6];                                   // bg, lam, sigma, E, f_AA, f_DD
@@ -180,152 +213,212 @@ __global__ void __launch_bounds__(kThreads) erk_kernel_pool(const OdeArgs a) {
     double yt[kNs];
     double k1[kOwn], k2[kOwn], k3[kOwn], k4[kOwn], k5[kOwn], k6[kOwn], k7[kOwn], yo[kOwn];
     double xo[kOwn];                                // the owner's components of x
+    // theta-dependent constants of problem f (after a set-up or a move)
+    auto derive = [&](const double *th, int p) {
+        make_slots(half, th, sl);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) fr[i] = th[30 + i];
+        st = a.sw_t + a.sw_off[p];
+        ns = a.sw_off[p + 1] - a.sw_off[p];
+        sv = a.sw_v + a.sw_off[p];
+        yp = a.y + static_cast<int64_t>(p) * a.K;
+        lnorm = -log(fr[2]) - 0.91893853320467274178;   // -log sigma - log(2 pi)/2
+    };
     for (;;) {
-        if (!busy) {
-            unsigned long long q = 0;
-            if (half == 0) q = atomicAdd(a.next, 1ull);
-            q = __shfl_sync(pmask, q, leader);
-            if (q >= static_cast<unsigned long long>(F)) break;
-            const int pi = static_cast<int>(q / static_cast<unsigned long long>(a.M));
-            const int p = a.porder[pi];
-            const int64_t m = static_cast<int64_t>(q) - static_cast<int64_t>(pi) * a.M;
-            f = m * a.NP + p;
-            double th[36];
-            bool ok = true;
-            for (int i = 0; i < 36; ++i) {
-                th[i] = a.thetas[m * 36 + i];
-                ok = ok && isfinite(th[i]) && th[i] > 0.0;
+        for (int trip = 0; trip < kEpoch; ++trip) {
+            if (!busy) {
+                if (drained) break;
+                unsigned long long q = 0;
+                if (half == 0) q = atomicAdd(a.next, 1ull);
+                q = __shfl_sync(pmask, q, leader);
+                if (q >= static_cast<unsigned long long>(F)) {
+                    drained = true;
+                    break;
+                }
+                const int pi = static_cast<int>(q / static_cast<unsigned long long>(a.M));
+                const int p = a.porder[pi];
+                const int64_t m = static_cast<int64_t>(q) - static_cast<int64_t>(pi) * a.M;
+                f = m * a.NP + p;
+                double th[36];
+                bool ok = true;
+                for (int i = 0; i < 36; ++i) {
+                    th[i] = a.thetas[m * 36 + i];
+                    ok = ok && isfinite(th[i]) && th[i] > 0.0;
+                }
+                ok = ok && th[33] < 1.0;            // FRET efficiency E in (0, 1)
+                if (!ok) {
+                    if (half == 0) {
+                        a.ll_f[f] = __longlong_as_double(0x7FF8000000000000ll);
+                        a.st_f[f] = PF_ST_INVALID_THETA;
+                        if (a.steps_f) a.steps_f[f] = 0;
+                    }
+                    continue;
+                }
+                const double y0[kNs] = {th[27], 0.0, 0.1, 0.0, 0.7, 0.0, 0.68, 0.0, 0.26, 0.0, th[28], 0.0,
+                                        th[29], th[29]};
+#pragma unroll
+                for (int c = 0; c < kNs; ++c) yt[c] = y0[c];
+#pragma unroll
+                for (int c = 0; c < kOwn; ++c) xo[c] = up ? (c < 6 ? yt[8 + c] : 0.0) : yt[c];
+                derive(th, p);
+                si = 0;                               // next switch index with st[si] > t
+                while (si < ns && st[si] <= 0.0) ++si;
+                u = 0.0;
+                for (int i = 0; i < ns && st[i] <= 0.0; ++i) u = sv[i];
+                t = 0.0;
+                h = 1e-3;
+                ll = 0.0;
+                steps = 0;
+                status = PF_ST_OK;
+                fresh = true;
+                k = 0;
+                busy = true;
             }
-            ok = ok && th[33] < 1.0;                // FRET efficiency E in (0, 1)
-            if (!ok) {
-                if (half == 0) {
-                    a.ll_f[f] = __longlong_as_double(0x7FF8000000000000ll);
-                    a.st_f[f] = PF_ST_INVALID_THETA;
-                    if (a.steps_f) a.steps_f[f] = 0;
+            const double tk = a.obs[k];
+            if (!(t < tk)) {                          // at observation time k
+                const double R = fret(yt, fr);       // yt = x after the last accepted step
+                const double z = (yp[k] - R) / fr[2];
+                ll += lnorm - 0.5 * z * z;
+                if (++k == a.K) {
+                    if (half == 0) {
+                        a.ll_f[f] = ll;
+                        a.st_f[f] = PF_ST_OK;
+                        if (a.steps_f) a.steps_f[f] = steps;
+                    }
+                    busy = false;
                 }
                 continue;
             }
-            const double y0[kNs] = {th[27], 0.0, 0.1, 0.0, 0.7, 0.0, 0.68, 0.0, 0.26, 0.0, th[28], 0.0,
-                                    th[29], th[29]};
+            // one Dormand-Prince step towards the next stop (input switch or observation)
+            const double tstop = (si < ns && st[si] < tk) ? st[si] : tk;
+            if (fresh) {
+                rhs_pair(up, sl, yt, u, k1);
+                fresh = false;
+            }
+            bool last = false;
+            double hh = h;
+            if (t + hh >= tstop) {
+                hh = tstop - t;
+                last = true;
+            }
 #pragma unroll
-            for (int c = 0; c < kNs; ++c) yt[c] = y0[c];
+            for (int c = 0; c < kOwn; ++c) yo[c] = xo[c] + hh * (A21 * k1[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k2);
 #pragma unroll
-            for (int c = 0; c < kOwn; ++c) xo[c] = up ? (c < 6 ? yt[8 + c] : 0.0) : yt[c];
-            make_slots(half, th, sl);
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] + hh * (A31 * k1[c] + A32 * k2[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k3);
 #pragma unroll
-            for (int i = 0; i < 6; ++i) fr[i] = th[30 + i];
-            st = a.sw_t + a.sw_off[p];
-            ns = a.sw_off[p + 1] - a.sw_off[p];
-            sv = a.sw_v + a.sw_off[p];
-            yp = a.y + static_cast<int64_t>(p) * a.K;
-            lnorm = -log(fr[2]) - 0.91893853320467274178;   // -log sigma - log(2 pi)/2
-            si = 0;                                   // next switch index with st[si] > t
-            while (si < ns && st[si] <= 0.0) ++si;
-            u = 0.0;
-            for (int i = 0; i < ns && st[i] <= 0.0; ++i) u = sv[i];
-            t = 0.0;
-            h = 1e-3;
-            ll = 0.0;
-            steps = 0;
-            status = PF_ST_OK;
-            fresh = true;
-            k = 0;
-            busy = true;
-        }
-        const double tk = a.obs[k];
-        if (!(t < tk)) {                              // at observation time k
-            const double R = fret(yt, fr);           // yt = x after the last accepted step
-            const double z = (yp[k] - R) / fr[2];
-            ll += lnorm - 0.5 * z * z;
-            if (++k == a.K) {
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] + hh * (A41 * k1[c] + A42 * k2[c] + A43 * k3[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k4);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] + hh * (A51 * k1[c] + A52 * k2[c] + A53 * k3[c] + A54 * k4[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k5);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] + hh * (A61 * k1[c] + A62 * k2[c] + A63 * k3[c] + A64 * k4[c] + A65 * k5[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k6);
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c)
+                yo[c] = xo[c] + hh * (B1 * k1[c] + B3 * k3[c] + B4 * k4[c] + B5 * k5[c] + B6 * k6[c]);
+            exchange(pmask, up, yo, yt);
+            rhs_pair(up, sl, yt, u, k7);
+            double err = 0.0;
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c) {
+                const double ei = hh * (E1 * k1[c] + E3 * k3[c] + E4 * k4[c] + E5 * k5[c] + E6 * k6[c] +
+                                        E7 * k7[c]);
+                const double sc = a.atol + a.rtol * fmax(fabs(xo[c]), fabs(yo[c]));
+                const double r = ei / sc;
+                if (!up || c < 6) err += r * r;
+            }
+            err += __shfl_xor_sync(pmask, err, 1);   // both halves, commutative: identical sums
+            err = sqrt(err / kNs);
+            if (!isfinite(err)) {
+                status = PF_ST_NONFINITE;
+            } else if (++steps > static_cast<uint32_t>(a.max_steps)) {
+                status = PF_ST_BUDGET;
+            } else if (err <= 1.0) {                  // accept
+                t = last ? tstop : t + hh;
+#pragma unroll
+                for (int c = 0; c < kOwn; ++c) xo[c] = yo[c];
+#pragma unroll
+                for (int c = 0; c < kOwn; ++c) k1[c] = k7[c];   // first same as last
+                const double fac = err > 0.0 ? fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2))) : 5.0;
+                if (!last || hh * fac < h) h = hh * fac;
+                if (last && si < ns && st[si] == tstop) {   // the input switches here
+                    while (si < ns && st[si] <= tstop) u = sv[si++];
+                    fresh = true;
+                }
+            } else {                                  // reject: shrink and retry
+                h = hh * fmax(0.2, 0.9 * pow(err, -0.2));
+            }
+            if (status != PF_ST_OK) {
                 if (half == 0) {
-                    a.ll_f[f] = ll;
-                    a.st_f[f] = PF_ST_OK;
+                    a.ll_f[f] = -INFINITY;
+                    a.st_f[f] = static_cast<uint8_t>(status);
                     if (a.steps_f) a.steps_f[f] = steps;
                 }
                 busy = false;
             }
-            continue;
         }
-        // one Dormand-Prince step towards the next stop (input switch or observation)
-        const double tstop = (si < ns && st[si] < tk) ? st[si] : tk;
-        if (fresh) {
-            rhs_pair(up, sl, yt, u, k1);
-            fresh = false;
+        // the block's barrier: end of the launch, or a move of the busy problems
+        if (drained) drained_s = 1;
+        __syncthreads();
+        const bool all_drained = drained_s != 0;
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, busy && half == 0);
+        if (lane == 0) warp_busy[warp] = __popc(bal);
+        __syncthreads();
+        int total = 0, used = 0, before = 0;
+#pragma unroll
+        for (int w = 0; w < kPackWarps; ++w) {
+            const int c = warp_busy[w];
+            total += c;
+            used += c > 0 ? 1 : 0;
+            before += w < warp ? c : 0;
         }
-        bool last = false;
-        double hh = h;
-        if (t + hh >= tstop) {
-            hh = tstop - t;
-            last = true;
-        }
+        if (all_drained && total == 0) break;         // the same decision in every thread
+        if (!all_drained || (total + 15) / 16 >= used) continue;
+        // pair r of the block takes the r-th busy problem (in pair order)
+        if (busy) {
+            Parked &P = park[before + __popc(bal & ((1u << leader) - 1u))];
 #pragma unroll
-        for (int c = 0; c < kOwn; ++c) yo[c] = xo[c] + hh * (A21 * k1[c]);
-        exchange(pmask, up, yo, yt);
-        rhs_pair(up, sl, yt, u, k2);
-#pragma unroll
-        for (int c = 0; c < kOwn; ++c)
-            yo[c] = xo[c] + hh * (A31 * k1[c] + A32 * k2[c]);
-        exchange(pmask, up, yo, yt);
-        rhs_pair(up, sl, yt, u, k3);
-#pragma unroll
-        for (int c = 0; c < kOwn; ++c)
-            yo[c] = xo[c] + hh * (A41 * k1[c] + A42 * k2[c] + A43 * k3[c]);
-        exchange(pmask, up, yo, yt);
-        rhs_pair(up, sl, yt, u, k4);
-#pragma unroll
-        for (int c = 0; c < kOwn; ++c)
-            yo[c] = xo[c] + hh * (A51 * k1[c] + A52 * k2[c] + A53 * k3[c] + A54 * k4[c]);
-        exchange(pmask, up, yo, yt);
-        rhs_pair(up, sl, yt, u, k5);
-#pragma unroll
-        for (int c = 0; c < kOwn; ++c)
-            yo[c] = xo[c] + hh * (A61 * k1[c] + A62 * k2[c] + A63 * k3[c] + A64 * k4[c] + A65 * k5[c]);
-        exchange(pmask, up, yo, yt);
-        rhs_pair(up, sl, yt, u, k6);
-#pragma unroll
-        for (int c = 0; c < kOwn; ++c)
-            yo[c] = xo[c] + hh * (B1 * k1[c] + B3 * k3[c] + B4 * k4[c] + B5 * k5[c] + B6 * k6[c]);
-        exchange(pmask, up, yo, yt);
-        rhs_pair(up, sl, yt, u, k7);
-        double err = 0.0;
-#pragma unroll
-        for (int c = 0; c < kOwn; ++c) {
-            const double ei = hh * (E1 * k1[c] + E3 * k3[c] + E4 * k4[c] + E5 * k5[c] + E6 * k6[c] +
-                                    E7 * k7[c]);
-            const double sc = a.atol + a.rtol * fmax(fabs(xo[c]), fabs(yo[c]));
-            const double r = ei / sc;
-            if (!up || c < 6) err += r * r;
-        }
-        err += __shfl_xor_sync(pmask, err, 1);       // both halves, commutative: identical sums
-        err = sqrt(err / kNs);
-        if (!isfinite(err)) {
-            status = PF_ST_NONFINITE;
-        } else if (++steps > static_cast<uint32_t>(a.max_steps)) {
-            status = PF_ST_BUDGET;
-        } else if (err <= 1.0) {                      // accept
-            t = last ? tstop : t + hh;
-#pragma unroll
-            for (int c = 0; c < kOwn; ++c) xo[c] = yo[c];
-#pragma unroll
-            for (int c = 0; c < kOwn; ++c) k1[c] = k7[c];   // first same as last
-            const double fac = err > 0.0 ? fmin(5.0, fmax(0.2, 0.9 * pow(err, -0.2))) : 5.0;
-            if (!last || hh * fac < h) h = hh * fac;
-            if (last && si < ns && st[si] == tstop) {   // the input switches here
-                while (si < ns && st[si] <= tstop) u = sv[si++];
-                fresh = true;
+            for (int c = 0; c < kOwn; ++c) {
+                P.xo[half][c] = xo[c];
+                P.k1[half][c] = k1[c];
             }
-        } else {                                      // reject: shrink and retry
-            h = hh * fmax(0.2, 0.9 * pow(err, -0.2));
-        }
-        if (status != PF_ST_OK) {
             if (half == 0) {
-                a.ll_f[f] = -INFINITY;
-                a.st_f[f] = static_cast<uint8_t>(status);
-                if (a.steps_f) a.steps_f[f] = steps;
+                P.t = t; P.h = h; P.ll = ll; P.u = u; P.f = f;
+                P.k = k; P.si = si; P.steps = static_cast<int32_t>(steps); P.fresh = fresh ? 1 : 0;
             }
-            busy = false;
         }
+        __syncthreads();
+        busy = pair < total;
+        if (busy) {
+            const Parked &P = park[pair];
+#pragma unroll
+            for (int c = 0; c < kOwn; ++c) {
+                xo[c] = P.xo[half][c];
+                k1[c] = P.k1[half][c];
+            }
+            t = P.t; h = P.h; ll = P.ll; u = P.u; f = P.f;
+            k = P.k; si = P.si; steps = static_cast<uint32_t>(P.steps); fresh = P.fresh != 0;
+            status = PF_ST_OK;
+            const int64_t m = f / a.NP;
+            const int p = static_cast<int>(f - m * a.NP);
+            double th[36];
+            for (int i = 0; i < 36; ++i) th[i] = a.thetas[m * 36 + i];
+            derive(th, p);
+            exchange(pmask, up, xo, yt);              // x after the last accepted step
+        }
+        __syncthreads();                              // park[] is free again
     }
 }
 
@@ -334,15 +427,8 @@ __global__ void __launch_bounds__(kThreads) erk_kernel_pool(const OdeArgs a) {
 // pattern; used when all problems are resident at once.  Both lanes of a pair take the
 // same decisions (the error norm is summed over both halves in either order,
 // which is commutative), so they stay converged; a row's result depends on
-// its own inputs only.
-//
-// MinBlocks = 0 leaves the register count to the compiler (no spills, 4 blocks
-// per SM); MinBlocks = 6 caps it so that 6 blocks fit (a few spills to L1).
-// The host takes the capped instance only when the whole grid then fits in
-// one wave and otherwise would not: a grid of fewer problems than the GPU
-// holds gains more from having all of them resident than the spills cost.
-template <int MinBlocks>
-__global__ void __launch_bounds__(kThreads, MinBlocks) erk_kernel_wave(const OdeArgs a) {
+// its own inputs only.  No register cap: 4 blocks per SM without spills.
+__global__ void __launch_bounds__(kThreads) erk_kernel_wave(const OdeArgs a) {
     const int64_t tg = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     const int64_t g = tg >> 1;
     const int half = static_cast<int>(tg & 1);
@@ -621,25 +707,19 @@ extern "C" int pf_erk_loglik(const double *thetas, int64_t M, const double *swit
     ODE_CUDA(b_ctr.alloc(sizeof(unsigned long long), s), "alloc work counter");
     ODE_CUDA(cudaMemsetAsync(b_ctr.p, 0, sizeof(unsigned long long), s), "clear work counter");
     a.next = static_cast<unsigned long long *>(b_ctr.p);
-    int dev = 0, sms = 0, occ_plain = 0, occ_capped = 0;
+    int dev = 0, sms = 0, occ_wave = 0, occ_pack = 0;
     ODE_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     ODE_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
-    int occ_pool = 0;
-    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_plain, pf::erk_kernel_wave<0>, pf::kThreads, 0),
+    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_wave, pf::erk_kernel_wave, pf::kThreads, 0),
              "occupancy");
-    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_capped, pf::erk_kernel_wave<6>, pf::kThreads, 0),
+    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pack, pf::erk_kernel_pack, pf::kPackThreads, 0),
              "occupancy");
-    ODE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_pool, pf::erk_kernel_pool, pf::kThreads, 0),
-             "occupancy");
-    // Problems that fit one resident wave run one per pair (the register-capped
-    // instance when the plain one would need a second wave); more problems run
+    // Problems that fit one resident wave run one per pair; more problems run
     // on persistent pairs that take them from a work counter.
-    if (nblk <= (int64_t)occ_plain * sms)
-        pf::erk_kernel_wave<0><<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
-    else if (nblk <= (int64_t)occ_capped * sms)
-        pf::erk_kernel_wave<6><<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
+    if (nblk <= (int64_t)occ_wave * sms)
+        pf::erk_kernel_wave<<<(unsigned)nblk, pf::kThreads, 0, s>>>(a);
     else
-        pf::erk_kernel_pool<<<(unsigned)((int64_t)std::max(1, occ_pool) * sms), pf::kThreads, 0, s>>>(a);
+        pf::erk_kernel_pack<<<(unsigned)((int64_t)std::max(1, occ_pack) * sms), pf::kPackThreads, 0, s>>>(a);
     ODE_CUDA(cudaGetLastError(), "ode launch");
     pf::erk_reduce_kernel<<<(unsigned)((M + 255) / 256), 256, 0, s>>>(a.ll_f, a.st_f, M, NP, d_ll, d_st);
     ODE_CUDA(cudaGetLastError(), "ode reduce launch");

@@ -48,4 +48,14 @@ __device__ __forceinline__ double scaled_u53(uint64_t v) {
     return __longlong_as_double(static_cast<long long>(bits));
 }
 
+// The same for 0 <= v <= 2^53, with 0 -> +0.0 chosen on the integer side (a
+// select of the bit pattern instead of a branch or a double-typed select).
+__device__ __forceinline__ double scaled_u53_or_zero(uint64_t v) {
+    const int e = 63 - __clzll(static_cast<long long>(v | 1ull));
+    const uint64_t mant = (e >= 52) ? (v >> (e - 52)) : (v << (52 - e));
+    const uint64_t bits = (static_cast<uint64_t>(e - 53 + 1023) << 52) |
+                          (mant & ((1ull << 52) - 1ull));
+    return __longlong_as_double(static_cast<long long>(v ? bits : 0ull));
+}
+
 }  // namespace pf

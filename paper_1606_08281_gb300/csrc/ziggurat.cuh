@@ -72,7 +72,7 @@ __device__ __forceinline__ double zig_exp(uint64_t first, uint32_t j, uint32_t p
         const int i = static_cast<int>(W & 0x7FFu);
         const uint64_t uv = W >> 11;
         const double xi = zx[i];
-        const double x = __dmul_rn(uv ? scaled_u53(uv) : 0.0, xi);
+        const double x = __dmul_rn(scaled_u53_or_zero(uv), xi);
         // both non-negative: compare as integers
         if (__double_as_longlong(x) < __double_as_longlong(zx[i + 1])) return x;
         // slow paths need the next word of the stream
@@ -88,7 +88,7 @@ __device__ __forceinline__ double zig_exp(uint64_t first, uint32_t j, uint32_t p
         }
         if (i == 0) return __dadd_rn(kZigR, neg_log_u53((W2 >> 11) + 1ull, log_table_global()));
         const uint64_t v2 = W2 >> 11;
-        const double U = v2 ? scaled_u53(v2) : 0.0;
+        const double U = scaled_u53_or_zero(v2);
         const ZigLayer &L = zg->layer[i];
         const double f = __ldg(&L.f);
         const double y = __dadd_rn(f, __dmul_rn(U, __ldg(&L.df)));
@@ -115,7 +115,7 @@ __device__ __forceinline__ double zig_exp(uint64_t first, uint32_t j, uint32_t p
 __device__ __forceinline__ bool zig_fast(uint64_t first, const double *zx, double &x) {
     const int i = static_cast<int>(first & 0x7FFu);
     const uint64_t uv = first >> 11;
-    x = __dmul_rn(uv ? scaled_u53(uv) : 0.0, zx[i]);
+    x = __dmul_rn(scaled_u53_or_zero(uv), zx[i]);
     return __double_as_longlong(x) < __double_as_longlong(zx[i + 1]);
 }
 

@@ -58,12 +58,13 @@ def calibrate_thresholds(stream, rows: int = 256) -> dict:
 
 
 def run_hetero(mix, n_slots: int = 3, repeats: int = 1, tune: bool = True,
-               tune_cache=None) -> dict:
+               tune_cache=None, tune_frac: float = 1 / 32) -> dict:
     """The mix as one batch of a context (persistent kernels, one graph replay)
     against plain per-request pf_loglik launches.  Requests whose filters
     cannot fill the GPU alone (autotune.split_rule) run split over thread-block
     clusters in both arms, with the same cluster size; the context's launch
-    shape comes from the batch autotuner on a sample of the mix (tune=True)."""
+    shape comes from the batch autotuner on a sample of the mix (tune=True:
+    tune_frac of every request's theta rows per candidate)."""
     from . import autotune
     names = sorted({s.problem for s in mix})
     wl = {n: W.get(n) for n in names}
@@ -86,7 +87,7 @@ def run_hetero(mix, n_slots: int = 3, repeats: int = 1, tune: bool = True,
     shapes = [(s.problem, 1 << int(np.ceil(np.log2(len(s.thetas)))), s.n_particles, s.K_use,
                bool(sp)) for s, sp in zip(mix, split)]
     if tune:
-        cfg = autotune.tune_batch(make, shapes, cache=tune_cache,
+        cfg = autotune.tune_batch(make, shapes, sample_frac=tune_frac, cache=tune_cache,
                                   load_problems=lambda c: _load_problems(c, names))
     else:
         cfg = {"block_threads": [128] * 4, "cluster_blocks": 4, "grab": 1}

@@ -124,22 +124,26 @@ def test_full_size_erk_sampled(pf):
         Rm = ode.observe(th[m], w.patterns, w.obs_times)
         tol = 100 * sum(tolerance(th[m], Rm[p], y[p]) for p in range(len(y))) + 1e-9 * abs(per.sum())
         assert abs(g["loglik"][m] - per.sum()) <= tol, (m, g["loglik"][m], per.sum(), tol)
-    # 4096 rows fit in one wave only with the register-capped kernel instance,
-    # 64 rows run on the uncapped one: the same rows give the same bits
+    # 4096 rows need more lane pairs than one wave holds and run on persistent
+    # pairs, 64 rows on one pair each: the same rows give the same bits
     sub = pf.pf_erk_loglik(th[:64], w.patterns, w.obs_times, y)
     assert np.array_equal(sub["loglik"], g["loglik"][:64])
 
 
 def test_persistent_pairs_equal_one_wave(pf):
-    """More problems than one resident wave (16 384 rows x 6 patterns) run on
-    persistent lane pairs fed by a work counter; each problem's result is the
-    one the one-wave kernel gives for the same row, bit for bit."""
+    """More problems than one resident wave (4096 and 16 384 rows x 6
+    patterns) run on persistent lane pairs fed by a work counter, the block
+    moving its busy problems onto its lowest pairs once the counter is
+    exhausted; each problem's result is the one the one-wave kernel gives for
+    the same row (3000 rows: 18 000 problems, one pair each), bit for bit."""
     w = W.erk()
     w.M = 16384
     th = w.thetas()
     y = w.observations()
-    big = pf.pf_erk_loglik(th, w.patterns, w.obs_times, y, diagnostics=True)
-    assert (big["status"] == 0).all()
-    small = pf.pf_erk_loglik(th[:4096], w.patterns, w.obs_times, y, diagnostics=True)
-    assert np.array_equal(big["loglik"][:4096], small["loglik"])
-    assert np.array_equal(big["steps"][:4096], small["steps"])
+    small = pf.pf_erk_loglik(th[:3000], w.patterns, w.obs_times, y, diagnostics=True)
+    assert (small["status"] == 0).all()
+    for M in (4096, 16384):
+        big = pf.pf_erk_loglik(th[:M], w.patterns, w.obs_times, y, diagnostics=True)
+        assert (big["status"] == 0).all()
+        assert np.array_equal(big["loglik"][:3000], small["loglik"]), M
+        assert np.array_equal(big["steps"][:3000], small["steps"]), M

@@ -71,3 +71,19 @@ def test_fsp_and_ode_arguments(pf):
     einval(pf, pf.pf_erk_loglik, e.thetas(2), e.patterns, np.r_[0.0, e.obs_times[1:]], y)
     einval(pf, pf.pf_erk_loglik, e.thetas(2), e.patterns, e.obs_times, y, rtol=2.0)
     einval(pf, pf.pf_erk_loglik, e.thetas(2), e.patterns, e.obs_times, y, rtol=1e-10, atol=-1.0)
+
+
+def test_batch_split_rule_and_cluster_share():
+    """Host rules of the batch engine's cluster split: a request splits when
+    its filters cannot fill one resident wave, and only if each block's share
+    of the population fits the context's cluster arena (the bytes
+    pf_ctx_config documents: ceil(N/C) (12 + 8U) + 16, plus 1 KB)."""
+    from paper_1606_08281_gb300 import autotune, pf
+    assert autotune.split_rule(152 * 4 - 1) and not autotune.split_rule(152 * 4)
+    arena = pf.PF_CTX_CLUSTER_ARENA
+    for N, C, U in [(4096, 2, 10), (4096, 4, 10), (200, 4, 9), (3, 4, 1), (4, 4, 1), (1000, 8, 16)]:
+        share = -(-N // C)
+        fits = N - (C - 1) * share >= 1 and share * (12 + 8 * U) + 16 + 1024 <= arena
+        assert pf.split_fits(N, C, U) == fits, (N, C, U)
+    assert not pf.split_fits(4096, 2, 10) and pf.split_fits(4096, 4, 10)
+    assert not pf.split_fits(3, 4, 1)       # a block would hold no particle
