@@ -251,15 +251,6 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N,
                 }
             }
             if (!active) continue;
-            // This draw's random words and the ziggurat's first attempt depend
-            // on the draw counter alone: computed first, they overlap with the
-            // propensities (used only if the step draws at all).
-            const Philox4 w = philox4x32_10(draws, j0 + static_cast<uint32_t>(L.j), lane, mrow,
-                                            key0, key1);
-            const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
-            const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
-            double E;
-            const bool fast = zig_fast(r0, sh.zig.x, E);
             int first_dep = 0;  // dependency lists: the first propensity this step recomputes
             if constexpr (kDepList || kHoist) {
                 // Each lane recomputes its own list of propensities: the fired
@@ -317,6 +308,17 @@ __device__ void ssa_interval(SharedHead &sh, int *xs, int Np, int N,
                     }
                 }
             }
+            // This draw's random words and the ziggurat's first attempt depend
+            // on the draw counter alone (used only if the step draws at all):
+            // placed here, in the straight-line code of the prefix sums and the
+            // division, the integer Philox rounds interleave with that FP64
+            // chain.
+            const Philox4 w = philox4x32_10(draws, j0 + static_cast<uint32_t>(L.j), lane, mrow,
+                                            key0, key1);
+            const uint64_t r0 = (static_cast<uint64_t>(w.w1) << 32) | w.w0;
+            const uint64_t r1 = (static_cast<uint64_t>(w.w3) << 32) | w.w2;
+            double E;
+            const bool fast = zig_fast(r0, sh.zig.x, E);
             double run;
             if constexpr (kDepList) {
                 // The prefix sums below the earliest recomputed propensity of
