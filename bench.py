@@ -71,9 +71,9 @@ ZIG_FLOPS = 1.0 + P_WEDGE * (7.0 + P_WEDGE_OPEN * FP64_FLOPS_EXP + 0.5) + P_TAIL
 
 # DRAM bytes per launch of the filter kernel on the 4096-theta gene-expression
 # workload: ncu dram__bytes_read.sum + dram__bytes_write.sum of the current
-# kernel on its 152-theta case (655 616 + 0 bytes, one launch) scaled by the
+# kernel on its 152-theta case (229 120 + 0 bytes, one launch) scaled by the
 # filters processed (x 4096/152).
-FILTER_TRAFFIC_BYTES = 655_616 * 4096 / 152
+FILTER_TRAFFIC_BYTES = 229_120 * 4096 / 152
 
 
 def flops_per_event(R: int) -> float:
