@@ -53,10 +53,11 @@ def plain(pf, w, th, N, seed, K):
 
 SPECS = [  # (problem, M, N, K, seed)
     ("birth_death", 37, 100, 20, 11),
-    ("gene_expression", 9, 1000, 12, 12),        # population on chip
-    ("gene_expression", 3, 2048, 6, 13),         # population in the global slab
+    ("gene_expression", 9, 1000, 12, 12),        # population in the small arena (4 blocks/SM)
+    ("gene_expression", 3, 2048, 6, 13),         # population in the large arena (2 blocks/SM)
     ("cascade", 2, 256, 4, 14),
-    ("cascade", 1, 600, 3, 15),                  # cascade in the global slab
+    ("cascade", 1, 600, 3, 15),                  # cascade in the large arena
+    ("cascade", 1, 2048, 3, 18),                 # cascade in a global slab (106 KB)
     ("birth_death", 1, 1, 5, 16),                # a single particle
     ("gene_expression", 0, 64, 5, 17),           # an empty request
 ]
@@ -164,8 +165,9 @@ def test_batch_early_rejection_matches_plain(pf, ctx, problems):
 
 def test_batch_covers_every_tier(pf):
     """Requests on networks of every kernel group (reaction tiers with state
-    in registers or in shared memory, and a global-slab population) in one
-    batch equal their plain calls bit for bit."""
+    in registers or in shared memory; populations in the small and the large
+    arena and in a global slab) in one batch equal their plain calls bit for
+    bit."""
     from test_gpu_parity import tier_problem
     c = pf.pf_ctx_create(mem_budget_bytes=0, n_slots=2, max_particles=8192)
     try:
@@ -193,8 +195,8 @@ def oracle_rows(w, th, N, seed, K, ids=None):
 
 def test_batch_matches_the_oracle(pf, ctx, problems):
     """The context's results against the oracle directly (not only against
-    pf_loglik): every network, on-chip and global-slab populations, requests
-    with theta id bases."""
+    pf_loglik): every network, populations in both shared-memory arenas,
+    requests with theta id bases."""
     specs = [("birth_death", 25, 100, 20, 61, 0), ("gene_expression", 6, 1000, 10, 62, 500),
              ("gene_expression", 2, 2048, 5, 63, 0), ("cascade", 2, 256, 4, 64, 9000)]
     reqs = []
