@@ -87,3 +87,44 @@ def test_batch_split_rule_and_cluster_share():
         assert pf.split_fits(N, C, U) == fits, (N, C, U)
     assert not pf.split_fits(4096, 2, 10) and pf.split_fits(4096, 4, 10)
     assert not pf.split_fits(3, 4, 1)       # a block would hold no particle
+
+
+def test_batch_tuner_coordinate_descent_and_cache(monkeypatch, tmp_path):
+    """tune_batch's host logic with the context calls faked: it times every
+    block-size pair, then the other cluster size (only when the mix has split
+    requests) and the other grab, keeps the fastest, and a second call with the
+    same mix signature comes from the cache without timing anything."""
+    from paper_1606_08281_gb300 import autotune, pf
+    cost = {(64, 128): 1.0, (128, 128): 2.0, (64, 64): 3.0, (128, 64): 4.0}
+    made = []
+
+    def fake_create(budget, slots, max_particles, block_threads, cluster_blocks, grab):
+        made.append((tuple(block_threads), cluster_blocks, grab))
+        return len(made)
+
+    monkeypatch.setattr(pf, "pf_ctx_create_config", fake_create)
+    monkeypatch.setattr(pf, "pf_ctx_destroy", lambda c: None)
+    clock = {"t": 0.0}
+    monkeypatch.setattr(pf, "pf_ctx_run_batch", lambda c, reqs: clock.__setitem__(
+        "t", clock["t"] + reqs[0]))
+    monkeypatch.setattr(autotune.time, "perf_counter", lambda: clock["t"])
+
+    def make(ctx, ids, frac, cluster):
+        bt, cb, gr = made[ctx - 1]
+        t = cost[(bt[0], bt[1])] + (0.5 if cb == 2 else 0.0) - (0.25 if gr == 4 else 0.0)
+        return [t * frac / 0.125]
+
+    shapes = [("gene_expression", 64, 1000, 50, True)]
+    cache = tmp_path / "tune.json"
+    cfg = autotune.tune_batch(make, shapes, cache=cache, load_problems=lambda c: {})
+    assert cfg["block_threads"] == [64, 128, 128, 128]
+    assert cfg["cluster_blocks"] == 4 and cfg["grab"] == 4
+    assert len(cfg["timings_s"]) == 6          # 4 block pairs, cluster 2, grab 4
+    n = len(made)
+    again = autotune.tune_batch(make, shapes, cache=cache, load_problems=lambda c: {})
+    assert again == cfg and len(made) == n
+    # no split request: the cluster size is not tried
+    made.clear()
+    cfg2 = autotune.tune_batch(make, [("cascade", 8, 512, 100, False)], cache=None,
+                               load_problems=lambda c: {})
+    assert not any(k.startswith("cluster") for k in cfg2["timings_s"])
