@@ -59,6 +59,16 @@
  *     rounded to multiples of 2^-20 (so that a last-place difference between
  *     two logarithm implementations cannot move every quantised weight); the
  *     likelihood itself uses the unrounded log-weights.
+ *
+ * Pins (tests/test_oracle_pins.py, test_oracle_fsp.py, test_oracle_mutants.py):
+ * Philox known answers, the birth-death model's closed-form transient and
+ * stationary laws and its exact likelihood, conservation laws, the weight and
+ * log-sum-exp special cases (C = 0, N = 1), exact resampling counts, the
+ * exactness of grid20 and of the integer weights, and unbiasedness for
+ * exp(L_FSP) on gene expression and on a three-species second-order network.
+ * The full likelihood of the 10-species cascade workload is parity unpinned
+ * beyond these ingredients and the invariants: no FSP box of that dimension
+ * fits in memory.
  */
 #include <math.h>
 #include <stdint.h>
