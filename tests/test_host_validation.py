@@ -128,3 +128,24 @@ def test_batch_tuner_coordinate_descent_and_cache(monkeypatch, tmp_path):
     cfg2 = autotune.tune_batch(make, [("cascade", 8, 512, 100, False)], cache=None,
                                load_problems=lambda c: {})
     assert not any(k.startswith("cluster") for k in cfg2["timings_s"])
+
+
+def test_heterogeneous_mix_composition():
+    """The batched-launch mix: 64 seeded requests over the three networks with
+    theta counts, particle counts and observation prefixes in their stated
+    ranges, plus one Lac-Gfp request of the workload's first 32 rows; the same
+    seed gives the same mix."""
+    mix = W.hetero_mix()
+    assert len(mix) == 65
+    lac = [s for s in mix if s.problem == "lac_gfp"]
+    assert len(lac) == 1 and len(lac[0].thetas) == 32 and lac[0].n_particles == 200
+    assert np.array_equal(lac[0].thetas, W.lac_gfp().thetas(32))
+    for s in mix[:-1]:
+        assert s.problem in ("birth_death", "gene_expression", "cascade")
+        assert 1 <= len(s.thetas) <= 4096
+        assert s.n_particles in (256, 512, 1024, 2048, 4096)
+        assert 10 <= s.K_use <= 100 and s.K_use <= W.get(s.problem).K
+    again = W.hetero_mix()
+    assert all(np.array_equal(a.thetas, b.thetas) and a.seed == b.seed for a, b in zip(mix, again))
+    small = W.hetero_mix(n_requests=48, max_theta_cascade=64)
+    assert all(len(s.thetas) <= 64 for s in small if s.problem == "cascade")
